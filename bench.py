@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: Y = mask(P) * (H P), P^T Y and P^T P.
+
+One step = fe_apply_H + fe_gram_PtY + fe_gram_PtP on the paper-scale p=2
+workload (64x40x40 Q2 cells, 846,369 DoFs x 320 orbitals in 38 column
+blocks, ~20% block fill), FP32 cell arithmetic with FP64 Gram accumulation;
+the FP64 path is timed beside it.  Inputs are resident in HBM when the timed
+region starts; P and Y (215 MB each in FP32) are larger than L2, so no flush
+is needed between steps.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·P DoF·columns/s + Gram GFLOP/s, FP32-mixed vs FP64 at tol; p50/p99"
+UNIT = "DoF*columns/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="p2")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-blocks", type=int, default=8, help="column blocks in the CPU oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, n_blocks, fp32=True):
+    """Times the FP64 oracle (assembled SpMM restricted to the pattern, then
+    P^T Y and P^T P) on the first `n_blocks` column blocks of the workload.
+    Assembly of the rows it needs is timed separately."""
+    import numpy as np
+    from oracle import fe_oracle as O
+    from synth import inputs
+    mesh = O.BoxMesh.from_config(cfg)
+    blk = O.Blocking(mesh)
+    centres = inputs.orbital_centres(cfg)
+    perm, ptr = O.column_blocks(blk, centres, cfg.n_col_blocks)
+    pick = list(range(min(n_blocks, len(ptr) - 1)))
+    orbs = {int(perm[j]) for c in pick for j in range(ptr[c], ptr[c + 1])}
+    mv = O.build_orbitals(mesh, cfg, centres, round_fp32=fp32, orbitals=orbs)
+    pat = O.block_pattern(blk, mv, perm, ptr)
+    cb_of_orb = O.entry_mask(blk, pat, perm, ptr)
+    rows = np.nonzero(pat[:, pick].any(1))[0]
+    keys = np.nonzero(np.isin(blk.owner_rank(np.arange(mesh.n_nodes)), rows))[0]
+    cells = O.mesh_cells_touching(mesh, keys)
+    t0 = time.perf_counter()
+    H = O.assemble(mesh, O.potential_fn(cfg, fp32), cells=cells)
+    t_asm = time.perf_counter() - t0
+    Psp = O.sparse_multivector(mesh, mv)
+    t0 = time.perf_counter()
+    Y = O.apply_masked(H, Psp, blk, pat, cb_of_orb)
+    O.gram(Psp, Y)
+    O.gram(Psp, Psp)
+    t_run = time.perf_counter() - t0
+    ncols = len(orbs)
+    return {"value": mesh.n_nodes * ncols / t_run, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {len(pick)} of {len(ptr) - 1} column blocks ({ncols} of {len(perm)} "
+                      f"columns), all their pattern rows; FP64 scipy SpMM + Gram; assembly of the "
+                      f"needed rows ({len(cells)} cells) timed apart: {t_asm:.2f} s",
+            "seconds": t_run, "assembly_s": t_asm}
+
+
+def run_reference(args):
+    rank, world, _ = dist_init(args.gpus)
+    if rank != 0:
+        return
+    from synth import inputs
+    cfg = inputs.get_config(args.config)
+    times, vals = [], []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(cfg, 1)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+            vals.append(r["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_name(cfg)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _workload_name(cfg):
+    n = (cfg.p * cfg.nx + 1) * (cfg.p * cfg.ny + 1) * (cfg.p * cfg.nz + 1)
+    return (f"{cfg.name}: {cfg.nx}x{cfg.ny}x{cfg.nz} Q{cfg.p} cells, {n:,} DoFs x {cfg.n_orb} orbitals "
+            f"in {cfg.n_col_blocks} column blocks, ~{int(round(100 * (cfg.target_fill or 0)))}% block fill")
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def probe_alu(dtype):
+    import ctypes as C
+    from paper_1907_01005_gb300 import _capi
+    f = C.c_double()
+    _capi.check(_capi.fe_probe_fma(dtype, 4000 if dtype == 1 else 200, C.byref(f), C.c_void_p(0)))
+    return f.value
+
+
+def time_path(pb, steps, warmup):
+    """Per-step CUDA-event times (ms) of the three calls on the current stream."""
+    import torch
+    from paper_1907_01005_gb300 import apply_H, gram_PtP, gram_PtY
+    d = pb.dev
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        apply_H(pb.mesh, pb.P, pb.Y, s)
+        gram_PtY(pb.P, pb.Y, d["G_PY"], s)
+        gram_PtP(pb.P, d["G_PP"], s)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        e = ev[k]
+        e[0].record(s)
+        apply_H(pb.mesh, pb.P, pb.Y, s)
+        e[1].record(s)
+        gram_PtY(pb.P, pb.Y, d["G_PY"], s)
+        e[2].record(s)
+        gram_PtP(pb.P, d["G_PP"], s)
+        e[3].record(s)
+    torch.cuda.synchronize()
+    total = ev[0][0].elapsed_time(ev[-1][3])
+    per = {"apply": [e[0].elapsed_time(e[1]) for e in ev],
+           "gram_py": [e[1].elapsed_time(e[2]) for e in ev],
+           "gram_pp": [e[2].elapsed_time(e[3]) for e in ev],
+           "step": [e[0].elapsed_time(e[3]) for e in ev]}
+    return total, per
+
+
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_1907_01005_gb300 import FE_F32, FE_F64, apply_H_gram_host, harness
+    from synth import inputs
+    cfg = inputs.get_config(args.config)
+
+    pb = harness.build_problem(cfg, FE_F32)
+    harness.to_device(pb)
+    N, M = pb.mesh.n_dofs, pb.n_cols
+    info = pb.P.info
+    hbm_peak, peak_src = load_peaks()
+    fp32_peak = probe_alu(1)
+    fp64_peak = probe_alu(2)
+
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, per = time_path(pb, args.steps, args.warmup)
+    clk = clocks.stop()
+    barrier(world)
+    if pb.mesh.check_device() != 0:
+        raise RuntimeError("device status word set during the timed region")
+    ms_step = max_over_ranks(total_ms / args.steps, world)
+    value = world * N * M / (ms_step * 1e-3)
+
+    # algorithmic work per launch
+    s = 4
+    n_q = int(pb.mesh.info.n_q)
+    apply_bytes = 2 * info.n_values * s + n_q * s
+    gram_bytes = 2 * info.n_values * s
+    n = cfg.p + 1
+    apply_flops = info.active_cell_cols * (18 * n ** 4 + 3 * n ** 3)
+    t_apply = statistics.median(per["apply"]) * 1e-3
+    t_py = statistics.median(per["gram_py"]) * 1e-3
+    t_pp = statistics.median(per["gram_pp"]) * 1e-3
+    kernels = {
+        "apply": {"ms_p50": 1e3 * t_apply, "ms_p99": pct(per["apply"], 0.99),
+                  "gbs": apply_bytes / t_apply / 1e9, "hbm_frac": apply_bytes / t_apply / 1e9 / hbm_peak,
+                  "gflops": apply_flops / t_apply / 1e9,
+                  "fp32_frac": apply_flops / t_apply / fp32_peak, "bytes": apply_bytes,
+                  "flops": apply_flops},
+        "gram_py": {"ms_p50": 1e3 * t_py, "gflops": info.gram_flops / t_py / 1e9,
+                    "fp64_frac": info.gram_flops / t_py / fp64_peak,
+                    "gbs": gram_bytes / t_py / 1e9},
+        "gram_pp": {"ms_p50": 1e3 * t_pp, "gflops": info.gram_flops / t_pp / 1e9,
+                    "fp64_frac": info.gram_flops / t_pp / fp64_peak},
+    }
+    dom = max(("apply", t_apply), ("gram_py", t_py), ("gram_pp", t_pp), key=lambda x: x[1])[0]
+    if dom == "apply":
+        roof = {"kernel": "apply", "bound": "hbm", "achieved": apply_bytes / t_apply / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "frac": apply_bytes / t_apply / 1e9 / hbm_peak,
+                "traffic": None, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "alu_frac": apply_flops / t_apply / fp32_peak}
+    else:
+        t = t_py if dom == "gram_py" else t_pp
+        roof = {"kernel": dom, "bound": "alu", "achieved": info.gram_flops / t / 1e12,
+                "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": info.gram_flops / t / fp64_peak,
+                "traffic": None, "peak_source": "measured FP64 FMA probe (fe_probe_fma)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": _workload_name(cfg), "dofs": N, "columns": M,
+                       "col_blocks": cfg.n_col_blocks, "block_fill": info.nnz_blocks / (pb.mesh.n_row_blocks * cfg.n_col_blocks),
+                       "stored_values": int(info.stored_entries), "tiles": int(info.n_tiles),
+                       "gram_accumulate": "f64", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (P and Y %.0f MB each)" % (info.n_values * 4 / 1e6)},
+            "p50_ms": pct(per["step"], 0.5), "p99_ms": pct(per["step"], 0.99),
+            "apply_dof_cols_per_s": N * M / t_apply,
+            "gram_gflops": {"PtY": info.gram_flops / t_py / 1e9, "PtP": info.gram_flops / t_pp / 1e9},
+            "kernels": kernels, "roofline": roof,
+            "alu_peaks_tflops": {"fp32": fp32_peak / 1e12, "fp64": fp64_peak / 1e12},
+            "gpu_launches": 3 * args.steps, "clocks": clk}
+
+    # FP64 path on the same workload
+    if not args.no_fp64:
+        pb64 = harness.build_problem(cfg, FE_F64)
+        harness.to_device(pb64)
+        k64 = max(3, args.steps // 5)
+        tot64, per64 = time_path(pb64, k64, max(3, args.warmup // 2))
+        ms64 = max_over_ranks(tot64 / k64, world)
+        line["fp64"] = {"ms_per_step": ms64, "value": world * N * M / (ms64 * 1e-3),
+                        "apply_ms": statistics.median(per64["apply"]),
+                        "gram_py_ms": statistics.median(per64["gram_py"]),
+                        "gram_pp_ms": statistics.median(per64["gram_pp"]),
+                        "mixed_speedup": ms64 / ms_step}
+        del pb64
+        torch.cuda.empty_cache()
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    if not args.no_e2e:
+        d = pb.dev
+        Ph = torch.from_numpy(pb.P_host).pin_memory()
+        Yh = torch.empty_like(Ph).pin_memory()
+        Gh1 = torch.empty((M, M), dtype=torch.float64).pin_memory()
+        Gh2 = torch.empty((M, M), dtype=torch.float64).pin_memory()
+        s = torch.cuda.current_stream()
+        for _ in range(2):
+            apply_H_gram_host(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], Ph, Yh, Gh1, Gh2, s)
+        k = max(3, args.steps // 3)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(k):
+            apply_H_gram_host(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], Ph, Yh, Gh1, Gh2, s)
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / k, world)
+        line["e2e"] = {"value": world * N * M / t_e2e, "unit": UNIT,
+                       "h2d_bytes_per_step": int(info.value_bytes),
+                       "d2h_bytes_per_step": int(info.value_bytes + 2 * M * M * 8),
+                       "ms_per_step": 1e3 * t_e2e}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_sample(cfg, args.cpu_blocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * fe_mf.h -- C ABI of the GB300 matrix-free BCSR Hamiltonian library.
+ *
+ * The library applies the finite-element Hamiltonian H = -1/2 Laplacian + V(x)
+ * (Sec. 2; Eq. fe_matrices, Sec. 3.1) matrix-free to a block-sparse (BCSR)
+ * multivector P of localised orbitals on a box mesh of hexahedral Q_p cells,
+ * giving Y = H P restricted to P's block pattern (Alg. 6, Sec. 3.5), and forms
+ * the Gram products P^T Y and P^T P (Alg. 8, Sec. 3.6; Eqs. inner1/inner2).
+ *
+ * Conventions that hold for every entry point
+ * -------------------------------------------
+ * - Every function returns an int status: FE_OK (0) or a negative FE_E* code.
+ *   On error a message is stored in a thread-local buffer, readable with
+ *   fe_last_error().  No function aborts the process.
+ * - Handles (fe_mesh, fe_bcsr) are opaque, created and destroyed by the
+ *   library.  They are not thread-safe: one handle is used by one host
+ *   thread at a time.
+ * - Device memory is owned by the caller.  Entry points that take a device
+ *   pointer document how long the library keeps it: a pointer passed to a
+ *   *_bind / *_upload / fe_mesh_set_potential call is kept by the handle until
+ *   the handle is destroyed or re-bound, and must stay valid that long.
+ * - `stream` is a cudaStream_t (CUstream) passed as void*; NULL means the
+ *   legacy default stream.  Device work is enqueued on it and the call returns
+ *   without synchronising, unless a function says otherwise.
+ * - Host arrays are read during the call only and never kept.
+ *
+ * Mesh, numbering and blocking
+ * ----------------------------
+ * The mesh is a box of nx*ny*nz axis-aligned cells of edge hx*hy*hz with
+ * Lagrange Q_p elements; nodes sit on the lattice (p nx + 1)(p ny + 1)(p nz + 1)
+ * at x = h (cell + xi_k), xi the Gauss-Lobatto-Legendre points on [0,1].
+ * Row blocks follow Alg. 1 with 2x2x2-cell patches as the coarse cells:
+ * patches are ordered along a Morton curve (x in the lowest bit of each bit
+ * triple), and row block r holds the nodes of the patch of rank r that no
+ * earlier patch holds, i.e. every node belongs to the component-wise lowest
+ * patch that contains it.  Inside a row block, DoFs are numbered
+ * lexicographically (x fastest) over the patch-local lattice.
+ * Homogeneous Dirichlet (dirichlet=1): boundary nodes keep their DoF ids; the
+ * operator treats their input values as zero and writes zero to their rows.
+ */
+#ifndef FE_MF_H
+#define FE_MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FE_OK 0
+#define FE_EINVAL (-1)      /* an argument is out of range or NULL */
+#define FE_ENOMEM (-2)      /* host allocation failed, or a buffer is too small */
+#define FE_EPATTERN (-3)    /* a block pattern is malformed or two patterns differ */
+#define FE_ECUDA (-4)       /* a CUDA runtime call failed (message has the CUDA error) */
+#define FE_EDEVICE (-5)     /* a kernel reported an error through the device status word */
+#define FE_ESTATE (-6)      /* the handle is not in the state the call needs (e.g. not bound) */
+#define FE_EUNSUPPORTED (-7)/* valid but not supported by this build (e.g. degree p > 4 on the GPU) */
+
+#define FE_F32 1            /* FP32 storage, FP32 cell arithmetic, FP64 Gram accumulation */
+#define FE_F64 2            /* FP64 storage and arithmetic throughout */
+
+typedef struct fe_mesh fe_mesh;
+typedef struct fe_bcsr fe_bcsr;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int fe_version(void);
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to n bytes).  Returns FE_OK. */
+int fe_last_error(char* buf, size_t n);
+
+/* ------------------------------------------------------------------------
+ * Mesh and DoF map (Sec. 3.1; Alg. 1)
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t nx, ny, nz;           /* cells per direction (even) */
+    int32_t p;                    /* polynomial degree */
+    int32_t dirichlet;            /* 1: homogeneous Dirichlet on all six faces */
+    int32_t npx, npy, npz;        /* patches (row blocks) per direction */
+    int32_t lx, ly, lz;           /* lattice nodes per direction */
+    int32_t n_row_blocks;         /* = npx*npy*npz */
+    int32_t max_rows_per_block;   /* largest row block */
+    int32_t nq1;                  /* Gauss points per direction (= p+1) */
+    int64_t n_dofs;               /* = lx*ly*lz */
+    int64_t n_cells;
+    int64_t n_q;                  /* quadrature points = n_cells * nq1^3 */
+    double hx, hy, hz;
+} fe_mesh_info_t;
+
+/* Creates the box mesh, its patch order and DoF numbering (Alg. 1 reading
+ * above).  nx, ny, nz: even, >= 2; h*: > 0; p: 1..6 on the host, 1..4 on the
+ * GPU; dirichlet: 0 or 1.  FE_EINVAL on bad arguments. */
+int fe_mesh_create(int32_t nx, int32_t ny, int32_t nz, double hx, double hy, double hz,
+                   int32_t p, int32_t dirichlet, fe_mesh** out);
+int fe_mesh_destroy(fe_mesh* mesh);
+int fe_mesh_get_info(const fe_mesh* mesh, fe_mesh_info_t* info);
+
+/* rb_ptr[n_row_blocks+1]: DoFs of row block r are [rb_ptr[r], rb_ptr[r+1]). */
+int fe_mesh_row_blocks(const fe_mesh* mesh, int64_t* rb_ptr);
+
+/* pxyz[3*n_row_blocks]: patch coordinates (px, py, pz) of row block r. */
+int fe_mesh_patch_coords(const fe_mesh* mesh, int32_t* pxyz);
+
+/* ijk[3*n_dofs]: lattice coordinates (I, J, K) of each DoF id. */
+int fe_mesh_dof_keys(const fe_mesh* mesh, int32_t* ijk);
+
+/* xyz[3*n_dofs]: physical coordinates of each DoF id (FP64). */
+int fe_mesh_node_coords(const fe_mesh* mesh, double* xyz);
+
+/* xyz[3*n_q]: physical Gauss points in the potential layout
+ * [row block r][cell c = cx + 2 cy + 4 cz of the patch][qz][qy][qx]. */
+int fe_mesh_quad_points(const fe_mesh* mesh, double* xyz);
+
+/* Bytes of device workspace the mesh needs (tables and the device status word). */
+int fe_mesh_workspace_bytes(const fe_mesh* mesh, size_t* bytes);
+
+/* Copies the mesh tables into the caller's device buffer `workspace_dev`
+ * (at least fe_mesh_workspace_bytes, 256-byte aligned) on `stream` and keeps
+ * the pointer.  FE_ENOMEM if `bytes` is too small; FE_ECUDA on copy failure. */
+int fe_mesh_upload(fe_mesh* mesh, void* workspace_dev, size_t bytes, void* stream);
+
+/* Registers the potential V at the Gauss points (Eq. fe_matrices: the
+ * N_i V N_j term): n_q values of type dtype (FE_F32 or FE_F64) on the device,
+ * in the layout of fe_mesh_quad_points.  The pointer is kept; one potential of
+ * each dtype can be registered. */
+int fe_mesh_set_potential(fe_mesh* mesh, const void* vq_dev, int32_t dtype);
+
+/* Reads and clears the device status word on `stream` (synchronises it).
+ * *code = 0 if no kernel reported an error.  Returns FE_EDEVICE if *code != 0. */
+int fe_mesh_check_device(fe_mesh* mesh, void* stream, int32_t* code);
+
+/* ------------------------------------------------------------------------
+ * Column blocking (Alg. 2) and the closed block pattern (Sec. 3.5)
+ * ------------------------------------------------------------------------ */
+
+/* Alg. 2 for one process: locates the cell that contains each centre
+ * (centres[3*n_cols], clamped into the box), sorts the columns by the position
+ * of that cell in the ordered cell list of Alg. 1 (ties by column id), and
+ * splits the sorted list into n_col_blocks contiguous groups whose sizes
+ * differ by at most one (the first n_cols mod n_col_blocks groups are one
+ * larger).  Outputs perm[n_cols] (new column j is old column perm[j]) and
+ * col_block_ptr[n_col_blocks+1].  Widths must stay <= 16 (FE_EINVAL). */
+int fe_column_blocks(const fe_mesh* mesh, int32_t n_cols, const double* centres,
+                     int32_t n_col_blocks, int32_t* perm, int32_t* col_block_ptr);
+
+/* Closed pattern of Sec. 3.5: given the support of each column block as a
+ * set of DoF ids (supp_dofs[supp_ptr[c] .. supp_ptr[c+1]), any order,
+ * duplicates allowed), block (r, c) is in the pattern iff row block r owns a
+ * node of a cell that contains a support DoF of c.  Writes row_ptr
+ * [n_row_blocks+1] and up to `capacity` column indices (ascending per row
+ * block), and *nnz_blocks.  If capacity is too small nothing but *nnz_blocks
+ * is written and FE_ENOMEM is returned, so a first call with capacity 0 sizes
+ * the second. */
+int fe_pattern_closed(const fe_mesh* mesh, int32_t n_col_blocks, const int64_t* supp_ptr,
+                      const int64_t* supp_dofs, int64_t* row_ptr, int32_t* col_idx,
+                      int64_t capacity, int64_t* nnz_blocks);
+
+/* ------------------------------------------------------------------------
+ * BCSR multivector (Sec. 3.3-3.4)
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n_cols, n_col_blocks, n_row_blocks, dtype;
+    int32_t max_width;            /* widest column block */
+    int32_t pad_;
+    int64_t nnz_blocks;           /* stored (row block, column block) blocks */
+    int64_t n_values;             /* value slots, padding included */
+    int64_t stored_entries;       /* sum over blocks of rows*width */
+    size_t value_bytes;           /* bytes of the value array */
+    size_t table_bytes;           /* bytes of the device tables (tiles, Gram lists) */
+    int64_t n_tiles;              /* (patch, column block) work items of the apply */
+    int64_t active_cell_cols;     /* sum over tiles of active cells * width */
+    int64_t n_gram_items_py;      /* work items of the P^T Y kernel */
+    int64_t n_gram_items_pp;      /* work items of the P^T P kernel */
+    double gram_flops;            /* sum_r sum_{c1,c2 in r} 2 rows_r w_c1 w_c2 (one product) */
+} fe_bcsr_info_t;
+
+/* Creates a BCSR multivector with n_cols columns split into column blocks
+ * col_block_ptr[n_col_blocks+1] (widths 1..16) and the block pattern
+ * row_ptr[n_row_blocks+1] / col_idx[nnz] (strictly ascending per row block,
+ * in range; FE_EPATTERN otherwise).  dtype: FE_F32 or FE_F64.
+ * Value layout: the blocks are stored one after another in CSR order; block
+ * (r, c) holds rows_r x w_c values row-major (row = DoF of the row block in
+ * its local order, column = column inside the block), and starts at an
+ * element offset that is a multiple of 16 bytes (fe_bcsr_block_offsets). */
+int fe_bcsr_create(const fe_mesh* mesh, int32_t n_cols, int32_t n_col_blocks,
+                   const int32_t* col_block_ptr, const int64_t* row_ptr, const int32_t* col_idx,
+                   int32_t dtype, fe_bcsr** out);
+int fe_bcsr_destroy(fe_bcsr* bcsr);
+int fe_bcsr_get_info(const fe_bcsr* bcsr, fe_bcsr_info_t* info);
+
+/* offsets[nnz_blocks]: element offset of the first value of each block, in
+ * CSR order. */
+int fe_bcsr_block_offsets(const fe_bcsr* bcsr, int64_t* offsets);
+
+/* Attaches the caller's device value array (value_bytes, 256-byte aligned)
+ * and, when the multivector is used as the source P of fe_apply_H /
+ * fe_gram_*, a device table buffer of table_bytes into which the tile and
+ * Gram work lists are copied on `stream` (tables_dev may be NULL for a
+ * destination Y).  Both pointers are kept until re-bound or destroyed. */
+int fe_bcsr_bind(fe_bcsr* bcsr, void* values_dev, void* tables_dev, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Hot path (Alg. 6, Alg. 8)
+ * ------------------------------------------------------------------------ */
+
+/* Y = mask(P) * (H P): Alg. 6 with the destination restricted to P's block
+ * pattern.  Zeroes Y, then runs the matrix-free cell operator (gather of the
+ * non-empty column blocks of each patch, sum-factorised values and gradients
+ * at the Gauss points, quadrature of 1/2 grad.grad + V, integration, and
+ * scatter-add into Y).  P and Y must have identical patterns and dtype
+ * (FE_EPATTERN), P must be bound with tables and Y with values (FE_ESTATE),
+ * the mesh uploaded and a potential of the same dtype registered (FE_ESTATE). */
+int fe_apply_H(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, void* stream);
+
+/* G = P^T Y (Alg. 8, Eq. inner2): dense n_cols x n_cols FP64, row-major, in
+ * the column order of the multivectors, zero where no row block holds both
+ * column blocks.  G_dev is caller-owned device memory (n_cols^2 doubles);
+ * it is overwritten.  Accumulation is FP64 whatever the dtype. */
+int fe_gram_PtY(const fe_bcsr* P, const fe_bcsr* Y, double* G_dev, void* stream);
+
+/* G = P^T P (Alg. 8 / Eq. inner1 with the Euclidean product), same layout;
+ * computed for column-block pairs c1 <= c2 and mirrored. */
+int fe_gram_PtP(const fe_bcsr* P, double* G_dev, void* stream);
+
+/* fe_apply_H, then fe_gram_PtY and fe_gram_PtP, on one stream. */
+int fe_apply_H_gram(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_PY_dev,
+                    double* G_PP_dev, void* stream);
+
+/* End-to-end variant for callers whose data lives in host memory: copies
+ * P's values from P_host (value_bytes) into P's bound device array, runs
+ * fe_apply_H_gram, copies Y's values to Y_host and both Gram matrices to
+ * G_PY_host / G_PP_host, and synchronises `stream`.  Host buffers should be
+ * pinned for full copy bandwidth. */
+int fe_apply_H_gram_host(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_PY_dev,
+                         double* G_PP_dev, const void* P_host, void* Y_host,
+                         double* G_PY_host, double* G_PP_host, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement helper (not part of the paper's method)
+ * ------------------------------------------------------------------------ */
+
+/* Runs an FMA-throughput probe of the given dtype on the current device
+ * (eight independent FMA chains per thread, 8 CTAs of 256 threads per SM,
+ * `iters` x 128 FMAs per chain) and returns the achieved flop/s (2 per FMA),
+ * the ALU peak used for the roofline of ALU-bound kernels.  Synchronises
+ * `stream`; uses a small stream-ordered allocation. */
+int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_MF_H */

@@ -274,13 +274,16 @@ def element_matrices(mesh: BoxMesh, Vq: np.ndarray | None, mass: bool = False):
     return lap[None] + pot
 
 
-def assemble(mesh: BoxMesh, Vfunc=None, mass: bool = False, chunk: int = 8192):
+def assemble(mesh: BoxMesh, Vfunc=None, mass: bool = False, chunk: int = 8192, cells=None):
     """Global CSR matrix over all lattice nodes (oracle numbering = lattice key),
-    with Dirichlet rows and columns removed (set to zero) when mesh.dirichlet."""
+    with Dirichlet rows and columns removed (set to zero) when mesh.dirichlet.
+    With `cells`, only those cells are summed (rows whose cells are all in
+    the subset are then complete)."""
     rows, cols, vals = [], [], []
     nn = (mesh.p + 1) ** 3
-    for s in range(0, mesh.n_cells, chunk):
-        cells = np.arange(s, min(s + chunk, mesh.n_cells), dtype=np.int64)
+    all_cells = np.arange(mesh.n_cells, dtype=np.int64) if cells is None else np.asarray(cells, np.int64)
+    for s in range(0, len(all_cells), chunk):
+        cells = all_cells[s:s + chunk]
         keys = mesh.cell_nodes(cells)                      # (C, nn)
         if mass:
             Ek = np.broadcast_to(element_matrices(mesh, None, mass=True), (len(cells), nn, nn))
@@ -412,14 +415,20 @@ class Multivector:
     vals: list          # list of float64 arrays
 
 
-def build_orbitals(mesh: BoxMesh, cfg, centres=None, round_fp32: bool = False) -> Multivector:
+def build_orbitals(mesh: BoxMesh, cfg, centres=None, round_fp32: bool = False,
+                   orbitals=None) -> Multivector:
     """Support = interior nodes with |x - c| <= R; values from the shared
-    generator at the oracle's own node coordinates."""
+    generator at the oracle's own node coordinates.  With `orbitals` (a set of
+    ids) the other orbitals are left empty."""
     from synth import inputs
     if centres is None:
         centres = inputs.orbital_centres(cfg)
     keys, vals = [], []
     for a in range(len(centres)):
+        if orbitals is not None and a not in orbitals:
+            keys.append(np.zeros(0, np.int64))
+            vals.append(np.zeros(0))
+            continue
         lo, hi = centres[a] - cfg.radius, centres[a] + cfg.radius
         ks = _ball_candidates(mesh, lo, hi)
         xyz = mesh.node_coords(ks)

@@ -1,0 +1,11 @@
+"""GB300-native matrix-free BCSR Hamiltonian (arXiv:1907.01005 hot path).
+
+The compute path is libfe_mf.so (hand-written CUDA for sm_103a behind a C
+ABI, include/fe_mf.h); this package is its ctypes binding.
+"""
+from ._capi import (FE_EDEVICE, FE_EINVAL, FE_ENOMEM, FE_EPATTERN, FE_ESTATE, FE_ECUDA,
+                    FE_EUNSUPPORTED, FE_F32, FE_F64, FE_OK, FeError, check, last_error, load)
+from .api import (BCSR, Mesh, apply_H, apply_H_gram, apply_H_gram_host, gram_PtP, gram_PtY)
+
+__all__ = ["Mesh", "BCSR", "apply_H", "gram_PtY", "gram_PtP", "apply_H_gram", "apply_H_gram_host",
+           "FeError", "FE_F32", "FE_F64", "load", "check", "last_error"]

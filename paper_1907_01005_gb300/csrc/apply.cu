@@ -1,0 +1,330 @@
+// Matrix-free application of H = -1/2 Laplacian + V to a BCSR multivector
+// (Alg. 6 with the destination restricted to the source pattern).
+//
+// One CTA processes one (patch, column block) tile: it gathers the patch's
+// (2p+1)^3 nodal values of the column block from up to eight stored blocks
+// (the patch's own row block and its seven lower neighbours, Alg. 4/5
+// semantics precomputed into the tile), runs the sum-factorised cell operator
+// on each of the patch's eight cells, accumulates the cell results into a
+// patch tensor in shared memory and scatter-adds the patch tensor into Y.
+//
+// Thread mapping: a thread owns one (cell, column, plane) triple.  A cell
+// column is an n^3 tensor (n = p+1); its n threads each hold an n x n plane in
+// registers, so the 1D contractions along the two in-plane directions are
+// register-only and the third direction is reached by an exchange through
+// shared memory (z-planes <-> y-planes).
+#include <cstdio>
+
+#include "fe_internal.h"
+
+namespace femf {
+namespace {
+
+template <int P>
+struct Geo {
+    static constexpr int N = P + 1;          // nodes / Gauss points per cell direction
+    static constexpr int NP = 2 * P + 1;     // patch nodes per direction
+    static constexpr int NPN = NP * NP * NP;
+    static constexpr int N3 = N * N * N;
+};
+
+// Row block slot and row index of patch-local node (i, j, k) of patch
+// (px, py, pz).  Along each axis: local index 0 of a patch that is not the
+// lowest belongs to the lower neighbour (where it is index 2p); a row block
+// of a patch at coordinate 0 also holds its index-0 nodes.
+template <int P>
+__device__ __forceinline__ void node_slot_row(int i, int j, int k, int px, int py, int pz,
+                                              int& slot, int& row) {
+    constexpr int Q = 2 * P;
+    int dx = (i == 0 && px > 0) ? 0 : 1;
+    int dy = (j == 0 && py > 0) ? 0 : 1;
+    int dz = (k == 0 && pz > 0) ? 0 : 1;
+    int ii = dx ? i : Q, jj = dy ? j : Q, kk = dz ? k : Q;
+    int qx = px - 1 + dx, qy = py - 1 + dy, qz = pz - 1 + dz;
+    int nxq = Q + (qx == 0), nyq = Q + (qy == 0);
+    int rx = ii - (qx == 0 ? 0 : 1), ry = jj - (qy == 0 ? 0 : 1), rz = kk - (qz == 0 ? 0 : 1);
+    slot = dx + 2 * dy + 4 * dz;
+    row = rx + nxq * (ry + nyq * rz);
+}
+
+__device__ __forceinline__ bool on_boundary(int I, int J, int K, int lx, int ly, int lz) {
+    return I == 0 || J == 0 || K == 0 || I == lx - 1 || J == ly - 1 || K == lz - 1;
+}
+
+__device__ __forceinline__ void atomic_add_shared(float* a, float v) { atomicAdd(a, v); }
+__device__ __forceinline__ void atomic_add_shared(double* a, double v) { atomicAdd(a, v); }
+
+// Threads per CTA are capped so that the per-thread planes (four n x n arrays)
+// stay in registers: 8 cells x 16 columns x n planes for p <= 2, half of that
+// for p >= 3.
+template <int P>
+constexpr int max_threads() { return (P >= 3 ? 4 : 8) * kMaxW * (P + 1); }
+
+template <typename T, int P>
+__global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const ApplyArgs<T> a) {
+    using G = Geo<P>;
+    constexpr int N = G::N, NP = G::NP, NPN = G::NPN, N3 = G::N3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wmax = a.wmax;
+    const int cpr = a.cells_per_round;
+    T* U = reinterpret_cast<T*>(smem_raw);          // [NPN][wmax] gathered input
+    T* Yp = U + NPN * wmax;                          // [NPN][wmax] accumulated output
+    T* exA = Yp + NPN * wmax;                        // [cpr*wmax][N3] exchange
+    T* exB = exA + cpr * wmax * N3;
+
+    const Tile& tile = a.tiles[blockIdx.x];
+    const int w = tile.width;
+    const int px = tile.pxyz & 1023, py = (tile.pxyz >> 10) & 1023, pz = tile.pxyz >> 20;
+    const int cellmask = tile.cellmask;
+    if (w > wmax || w < 1) {
+        if (threadIdx.x == 0) atomicExch(a.status, kDevBadTile);
+        return;
+    }
+    int64_t off[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) off[b] = tile.off[b];
+
+    // ---- gather (Alg. 6, read step) -------------------------------------
+    for (int e = threadIdx.x; e < NPN * wmax; e += blockDim.x) {
+        const int node = e / wmax, col = e - node * wmax;
+        T v = T(0);
+        if (col < w) {
+            const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
+            int slot, row;
+            node_slot_row<P>(i, j, k, px, py, pz, slot, row);
+            const bool bnd = a.dirichlet &&
+                on_boundary(2 * P * px + i, 2 * P * py + j, 2 * P * pz + k, a.lx, a.ly, a.lz);
+            if (off[slot] >= 0 && !bnd) v = a.P[off[slot] + (int64_t)row * w + col];
+        }
+        U[e] = v;
+        Yp[e] = T(0);
+    }
+    __syncthreads();
+
+    // ---- cell operator, cpr cells at a time ------------------------------
+    const int t = threadIdx.x % N;            // plane index
+    const int cc = threadIdx.x / N;           // cell-column slot in this round
+    const int col = cc % wmax;
+    const int cslot = cc / wmax;
+    const auto& K = a.k;
+    T* myA = exA + (size_t)cc * N3;
+    T* myB = exB + (size_t)cc * N3;
+
+    for (int c0 = 0; c0 < 8; c0 += cpr) {
+        const int cell = c0 + cslot;
+        const bool act = (cslot < cpr) && (col < w) && ((cellmask >> cell) & 1);
+        const int cx = cell & 1, cy = (cell >> 1) & 1, cz = (cell >> 2) & 1;
+        T pa[N][N], pb[N][N];
+        // z-plane t of nodal values: pa[j][i]
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    const int node = (cx * P + i) + NP * ((cy * P + j) + NP * (cz * P + t));
+                    pa[j][i] = U[node * wmax + col];
+                }
+            // interpolate along x then y: pa -> pb -> pa  (values at (q_x, q_y, node z=t))
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int q = 0; q < N; ++q) {
+                    T s = T(0);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) s = fma(K.S[q][i], pa[j][i], s);
+                    pb[j][q] = s;
+                }
+#pragma unroll
+            for (int q = 0; q < N; ++q)
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    T s = T(0);
+#pragma unroll
+                    for (int j = 0; j < N; ++j) s = fma(K.S[q][j], pb[j][i], s);
+                    pa[q][i] = s;
+                }
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) myA[(t * N + j) * N + i] = pa[j][i];
+        }
+        __syncthreads();
+        // y-own: thread t holds q_y = t; pa[k][i] = value at (q_x=i, q_y=t, node z=k)
+        T uq[N][N], z1[N][N];
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+#pragma unroll
+                for (int i = 0; i < N; ++i) pa[k][i] = myA[(k * N + t) * N + i];
+            // interpolate along z
+#pragma unroll
+            for (int q = 0; q < N; ++q)
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    T s = T(0);
+#pragma unroll
+                    for (int k = 0; k < N; ++k) s = fma(K.S[q][k], pa[k][i], s);
+                    uq[q][i] = s;
+                }
+            // quadrature: x and z Laplacian terms and the potential
+            const T* V = a.Vq + ((int64_t)tile.patch * 8 + cell) * N3;
+#pragma unroll
+            for (int kq = 0; kq < N; ++kq)
+#pragma unroll
+                for (int iq = 0; iq < N; ++iq) {
+                    T s = K.jxw * V[iq + N * (t + N * kq)] * uq[kq][iq];
+#pragma unroll
+                    for (int l = 0; l < N; ++l) s = fma(K.A[0][iq][l], uq[kq][l], s);
+#pragma unroll
+                    for (int l = 0; l < N; ++l) s = fma(K.A[2][kq][l], uq[l][iq], s);
+                    z1[kq][iq] = s;
+                }
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    myA[(k * N + t) * N + i] = uq[k][i];
+                    myB[(k * N + t) * N + i] = z1[k][i];
+                }
+        }
+        __syncthreads();
+        if (act) {
+            // z-own: thread t holds q_z = t; add the y Laplacian term
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    pa[j][i] = myA[(t * N + j) * N + i];   // u_q
+                    pb[j][i] = myB[(t * N + j) * N + i];   // partial sum
+                }
+#pragma unroll
+            for (int jq = 0; jq < N; ++jq)
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    T s = pb[jq][i];
+#pragma unroll
+                    for (int l = 0; l < N; ++l) s = fma(K.A[1][jq][l], pa[l][i], s);
+                    z1[jq][i] = s;
+                }
+            // integrate along x then y: z1 -> pb -> pa  (nodal x, nodal y, q_z = t)
+#pragma unroll
+            for (int jq = 0; jq < N; ++jq)
+#pragma unroll
+                for (int ia = 0; ia < N; ++ia) {
+                    T s = T(0);
+#pragma unroll
+                    for (int iq = 0; iq < N; ++iq) s = fma(K.Sb[ia][iq], z1[jq][iq], s);
+                    pb[jq][ia] = s;
+                }
+#pragma unroll
+            for (int ja = 0; ja < N; ++ja)
+#pragma unroll
+                for (int ia = 0; ia < N; ++ia) {
+                    T s = T(0);
+#pragma unroll
+                    for (int jq = 0; jq < N; ++jq) s = fma(K.Sb[ja][jq], pb[jq][ia], s);
+                    pa[ja][ia] = s;
+                }
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) myA[(t * N + j) * N + i] = pa[j][i];
+        }
+        __syncthreads();
+        if (act) {
+            // y-own: thread t holds nodal y = t; integrate along z and accumulate
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+#pragma unroll
+                for (int i = 0; i < N; ++i) pb[k][i] = myA[(k * N + t) * N + i];
+#pragma unroll
+            for (int ka = 0; ka < N; ++ka)
+#pragma unroll
+                for (int ia = 0; ia < N; ++ia) {
+                    T s = T(0);
+#pragma unroll
+                    for (int kq = 0; kq < N; ++kq) s = fma(K.Sb[ka][kq], pb[kq][ia], s);
+                    const int node = (cx * P + ia) + NP * ((cy * P + t) + NP * (cz * P + ka));
+                    atomic_add_shared(&Yp[node * wmax + col], s);
+                }
+        }
+        __syncthreads();
+    }
+
+    // ---- scatter-add (Alg. 6, write step) ---------------------------------
+    for (int e = threadIdx.x; e < NPN * wmax; e += blockDim.x) {
+        const int node = e / wmax, c = e - node * wmax;
+        if (c >= w) continue;
+        const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
+        int slot, row;
+        node_slot_row<P>(i, j, k, px, py, pz, slot, row);
+        const bool bnd = a.dirichlet &&
+            on_boundary(2 * P * px + i, 2 * P * py + j, 2 * P * pz + k, a.lx, a.ly, a.lz);
+        if (off[slot] >= 0 && !bnd) atomicAdd(&a.Y[off[slot] + (int64_t)row * w + c], Yp[e]);
+    }
+}
+
+template <typename T, int P>
+cudaError_t launch_p(const ApplyArgs<T>& a, cudaStream_t s) {
+    const size_t smem = apply_smem_bytes<T>(P, a.wmax, a.cells_per_round);
+    const int threads = apply_threads<T>(P, a.wmax, a.cells_per_round);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8]) {
+        cudaError_t e = cudaFuncSetAttribute(apply_plane_kernel<T, P>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set[sizeof(T) == 8] = true;
+    }
+    if (a.n_tiles == 0) return cudaSuccess;
+    apply_plane_kernel<T, P><<<(unsigned)a.n_tiles, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+size_t apply_smem_bytes(int p, int wmax, int cpr) {
+    const size_t np = 2 * p + 1, n = p + 1;
+    return (2 * np * np * np * wmax + 2 * (size_t)cpr * wmax * n * n * n) * sizeof(T);
+}
+
+int apply_max_threads(int p) {
+    switch (p) {
+        case 1: return max_threads<1>();
+        case 2: return max_threads<2>();
+        case 3: return max_threads<3>();
+        default: return max_threads<4>();
+    }
+}
+
+template <typename T>
+int apply_threads(int p, int wmax, int cpr) {
+    const int t = cpr * wmax * (p + 1);
+    return (t + 31) / 32 * 32;
+}
+
+template <typename T>
+cudaError_t launch_apply(int p, const ApplyArgs<T>& a, cudaStream_t s) {
+    switch (p) {
+        case 1: return launch_p<T, 1>(a, s);
+        case 2: return launch_p<T, 2>(a, s);
+        case 3: return launch_p<T, 3>(a, s);
+        case 4: return launch_p<T, 4>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_apply<float>(int, const ApplyArgs<float>&, cudaStream_t);
+template cudaError_t launch_apply<double>(int, const ApplyArgs<double>&, cudaStream_t);
+template size_t apply_smem_bytes<float>(int, int, int);
+template size_t apply_smem_bytes<double>(int, int, int);
+template int apply_threads<float>(int, int, int);
+template int apply_threads<double>(int, int, int);
+
+}  // namespace femf

@@ -1,0 +1,111 @@
+// Internal declarations shared by the host builder (host.cpp) and the CUDA
+// kernels (apply.cu, gram.cu).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fe_mf.h"
+
+namespace femf {
+
+constexpr int kMaxP = 4;            // highest degree with GPU kernels
+constexpr int kMaxN = kMaxP + 1;    // 1D points per cell
+constexpr int kMaxW = 16;           // widest column block
+
+// 1D operators of the sum-factorised cell kernel on the reference cell
+// [0,1]^3 with n = p+1 Gauss points per direction (Sec. 3.2):
+//   S[q][a]  = l_a(x_q)              nodal basis (GLL nodes) at Gauss point q
+//   Sb[a][q] = S[q][a] * w_q         transposed interpolation with the weight
+//   A[d][l][m] = c_d (D^T W D)[l][m] / w_l,  c_d = |J| / (2 h_d^2)
+// where D is the collocation derivative on the Gauss points.  With these, the
+// cell operator on nodal values u reads
+//   y = Sb^3 [ sum_d A_d u_q + |J| V_q u_q ],   u_q = S^3 u,
+// the weights w_i w_j w_k of the tensor rule being folded into Sb and A.
+template <typename T>
+struct CellConsts {
+    T S[kMaxN][kMaxN];
+    T Sb[kMaxN][kMaxN];
+    T A[3][kMaxN][kMaxN];
+    T jxw;       // |J| = hx hy hz
+};
+
+// One (patch, column block) work item of the apply.  Slot b = dx + 2 dy + 4 dz
+// names the row block of patch (px - 1 + dx, py - 1 + dy, pz - 1 + dz); off[b]
+// is the element offset of block (that row block, column block) in the value
+// array, or -1 when the block is not stored (or the patch does not exist).
+struct Tile {
+    int64_t off[8];
+    int32_t patch;      // rank of the patch (= its row block)
+    int32_t pxyz;       // px | py << 10 | pz << 20
+    int32_t width;      // column block width
+    int32_t cellmask;   // bit c (c = cx + 2 cy + 4 cz) set iff that cell touches a stored block
+};
+
+// Gram work: entries are (block of A, block of B, rows) for one column-block
+// pair and one row block; items are contiguous entry ranges of one pair.
+struct GramEntry {
+    int64_t offA;
+    int64_t offB;
+    int32_t rows;
+    int32_t pad;
+};
+struct GramItem {
+    int32_t c1, c2;
+    int32_t begin, end;
+};
+
+template <typename T>
+struct ApplyArgs {
+    const T* P;
+    T* Y;
+    const T* Vq;
+    const Tile* tiles;
+    int64_t n_tiles;
+    int32_t npx, npy, npz;
+    int32_t lx, ly, lz;
+    int32_t dirichlet;
+    int32_t wmax;             // row stride of the patch tensors in shared memory
+    int32_t cells_per_round;  // cells processed concurrently (1, 2, 4 or 8)
+    int32_t* status;          // device status word (0 = ok)
+    CellConsts<T> k;
+};
+
+template <typename T>
+struct GramArgs {
+    const T* A;
+    const T* B;
+    const GramEntry* entries;
+    const GramItem* items;
+    int64_t n_items;
+    const int32_t* cb_ptr;
+    int32_t n_cols;
+    int32_t symmetric;        // 1: also write the mirrored block for c1 != c2
+    double* G;
+};
+
+// Launchers (apply.cu / gram.cu).  They return a cudaError_t and leave the
+// message to the caller.
+template <typename T>
+cudaError_t launch_apply(int p, const ApplyArgs<T>& a, cudaStream_t s);
+template <typename T>
+size_t apply_smem_bytes(int p, int wmax, int cells_per_round);
+template <typename T>
+int apply_threads(int p, int wmax, int cells_per_round);
+int apply_max_threads(int p);
+template <typename T>
+cudaError_t launch_gram(const GramArgs<T>& a, cudaStream_t s);
+
+cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s);
+
+// Device status codes written by kernels.
+enum DeviceStatus : int32_t {
+    kDevOk = 0,
+    kDevBadTile = 1,
+};
+
+}  // namespace femf

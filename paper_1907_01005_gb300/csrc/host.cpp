@@ -1,0 +1,877 @@
+// Host side of the library: mesh and DoF map (Alg. 1 reading), 1D operators
+// of the sum-factorised kernel, column blocking (Alg. 2), the closed block
+// pattern (Sec. 3.5), BCSR layout and work lists, and the C ABI entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "fe_internal.h"
+
+using namespace femf;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+namespace {
+
+thread_local char g_err[1024] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(FE_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define FE_TRY_CUDA(expr, what)                     \
+    do {                                            \
+        cudaError_t e_ = (expr);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// 1D points: Legendre polynomials by the three-term recurrence, Newton roots
+// ---------------------------------------------------------------------------
+void legendre(int n, double t, double& P, double& dP) {
+    double p0 = 1.0, p1 = t;
+    if (n == 0) { P = 1.0; dP = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        const double p2 = ((2 * k + 1) * t * p1 - k * p0) / (k + 1);
+        p0 = p1;
+        p1 = p2;
+    }
+    P = p1;
+    dP = n * (t * p1 - p0) / (t * t - 1.0);
+}
+
+// Gauss-Legendre points/weights on [0,1], ascending.
+void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double t = -std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double P, dP;
+            legendre(n, t, P, dP);
+            const double dt = P / dP;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        double P, dP;
+        legendre(n, t, P, dP);
+        x[i] = 0.5 * (t + 1.0);
+        w[i] = 1.0 / ((1.0 - t * t) * dP * dP);   // (2 / ((1-t^2) P'^2)) / 2
+    }
+}
+
+// Gauss-Lobatto-Legendre points on [0,1]: 0, 1 and the roots of P_p'.
+std::vector<double> gll_points(int p) {
+    std::vector<double> x(p + 1);
+    x[0] = 0.0;
+    x[p] = 1.0;
+    for (int j = 1; j < p; ++j) {
+        double t = -std::cos(M_PI * j / p);
+        for (int it = 0; it < 100; ++it) {
+            double P, dP;
+            legendre(p, t, P, dP);
+            // P'' from the Legendre equation (1-t^2) P'' - 2t P' + p(p+1) P = 0
+            const double d2P = (2.0 * t * dP - p * (p + 1.0) * P) / (1.0 - t * t);
+            const double dt = dP / d2P;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        x[j] = 0.5 * (t + 1.0);
+    }
+    return x;
+}
+
+uint64_t spread3(uint32_t v) {
+    uint64_t out = 0;
+    for (int b = 0; b < 21; ++b) out |= (uint64_t)((v >> b) & 1u) << (3 * b);
+    return out;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+struct fe_mesh {
+    int nx, ny, nz, p, dirichlet;
+    double h[3];
+    int np[3];
+    int L[3];
+    int n_patches;
+    int max_rows;
+    std::vector<int32_t> rank_to_pid, pid_to_rank;
+    std::vector<int64_t> rb_ptr;
+    std::vector<double> gll, gx, gw;
+    CellConsts<double> kd;
+    CellConsts<float> kf;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int32_t* status = nullptr;
+    const void* vq[2] = {nullptr, nullptr};   // FE_F32, FE_F64
+
+    int pid(int px, int py, int pz) const { return px + np[0] * (py + np[1] * pz); }
+    void pxyz(int id, int& px, int& py, int& pz) const {
+        px = id % np[0];
+        py = (id / np[0]) % np[1];
+        pz = id / (np[0] * np[1]);
+    }
+    int rows_of(int px, int py, int pz) const {
+        const int q = 2 * p;
+        return (q + (px == 0)) * (q + (py == 0)) * (q + (pz == 0));
+    }
+    // DoF id -> lattice coordinates (BlockIndices-style: upper_bound on rb_ptr)
+    void dof_ijk(int64_t dof, int& I, int& J, int& K) const {
+        const int r = int(std::upper_bound(rb_ptr.begin(), rb_ptr.end(), dof) - rb_ptr.begin()) - 1;
+        int px, py, pz;
+        pxyz(rank_to_pid[r], px, py, pz);
+        const int q = 2 * p;
+        const int nxq = q + (px == 0), nyq = q + (py == 0);
+        int64_t loc = dof - rb_ptr[r];
+        const int rx = int(loc % nxq);
+        loc /= nxq;
+        const int ry = int(loc % nyq);
+        const int rz = int(loc / nyq);
+        I = q * px + rx + (px == 0 ? 0 : 1);
+        J = q * py + ry + (py == 0 ? 0 : 1);
+        K = q * pz + rz + (pz == 0 ? 0 : 1);
+    }
+    int64_t dof_of_ijk(int I, int J, int K) const {
+        const int q = 2 * p;
+        const int px = std::max(0, (I - 1) / q), py = std::max(0, (J - 1) / q), pz = std::max(0, (K - 1) / q);
+        const int r = pid_to_rank[pid(px, py, pz)];
+        const int nxq = q + (px == 0), nyq = q + (py == 0);
+        const int rx = I - q * px - (px == 0 ? 0 : 1);
+        const int ry = J - q * py - (py == 0 ? 0 : 1);
+        const int rz = K - q * pz - (pz == 0 ? 0 : 1);
+        return rb_ptr[r] + rx + (int64_t)nxq * (ry + (int64_t)nyq * rz);
+    }
+    double coord(int d, int I) const {
+        const int n = d == 0 ? nx : (d == 1 ? ny : nz);
+        const int c = std::min(I / p, n - 1);
+        return h[d] * (c + gll[I - p * c]);
+    }
+};
+
+struct fe_bcsr {
+    const fe_mesh* mesh = nullptr;
+    int32_t n_cols = 0, ncb = 0, dtype = 0, wmax = 0;
+    std::vector<int32_t> cbp;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col_idx;
+    std::vector<int64_t> blk_off;
+    std::vector<int64_t> dense;          // [r * ncb + c] -> block index or -1
+    int64_t n_values = 0, stored = 0;
+    std::vector<Tile> tiles;
+    std::vector<GramEntry> e_py, e_pp;
+    std::vector<GramItem> i_py, i_pp;
+    size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
+    int64_t active_cell_cols = 0;
+    double gram_flops = 0.0;
+    uint64_t fingerprint = 0;
+    void* values = nullptr;
+    void* tables = nullptr;
+    size_t elem() const { return dtype == FE_F64 ? 8 : 4; }
+};
+
+namespace {
+
+void build_consts(fe_mesh& m) {
+    const int p = m.p, n = p + 1;
+    m.gll = gll_points(p);
+    gauss_rule(n, m.gx, m.gw);
+    CellConsts<double>& k = m.kd;
+    std::memset(&k, 0, sizeof(k));
+    // S[q][a] = l_a(x_q), l_a through the GLL nodes
+    for (int q = 0; q < n; ++q)
+        for (int a = 0; a <= p; ++a) {
+            double v = 1.0;
+            for (int m2 = 0; m2 <= p; ++m2)
+                if (m2 != a) v *= (m.gx[q] - m.gll[m2]) / (m.gll[a] - m.gll[m2]);
+            k.S[q][a] = v;
+        }
+    // collocation derivative on the Gauss points (barycentric form)
+    std::vector<double> lam(n, 1.0);
+    for (int j = 0; j < n; ++j)
+        for (int l = 0; l < n; ++l)
+            if (l != j) lam[j] /= (m.gx[j] - m.gx[l]);
+    std::vector<double> D(n * n, 0.0);
+    for (int q = 0; q < n; ++q)
+        for (int j = 0; j < n; ++j) {
+            if (q != j) {
+                D[q * n + j] = (lam[j] / lam[q]) / (m.gx[q] - m.gx[j]);
+            } else {
+                double s = 0.0;
+                for (int l = 0; l < n; ++l)
+                    if (l != q) s += 1.0 / (m.gx[q] - m.gx[l]);
+                D[q * n + q] = s;
+            }
+        }
+    const double jxw = m.h[0] * m.h[1] * m.h[2];
+    k.jxw = jxw;
+    for (int a = 0; a < n; ++a)
+        for (int q = 0; q < n; ++q) k.Sb[a][q] = k.S[q][a] * m.gw[q];
+    for (int d = 0; d < 3; ++d) {
+        const double c = 0.5 * jxw / (m.h[d] * m.h[d]);
+        for (int l = 0; l < n; ++l)
+            for (int j = 0; j < n; ++j) {
+                double s = 0.0;
+                for (int r = 0; r < n; ++r) s += D[r * n + l] * m.gw[r] * D[r * n + j];
+                k.A[d][l][j] = c * s / m.gw[l];
+            }
+    }
+    CellConsts<float>& f = m.kf;
+    for (int i = 0; i < kMaxN; ++i)
+        for (int j = 0; j < kMaxN; ++j) {
+            f.S[i][j] = float(k.S[i][j]);
+            f.Sb[i][j] = float(k.Sb[i][j]);
+            for (int d = 0; d < 3; ++d) f.A[d][i][j] = float(k.A[d][i][j]);
+        }
+    f.jxw = float(k.jxw);
+}
+
+uint64_t hash_mix(uint64_t h, uint64_t v) {
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int fe_version(void) { return 100; }
+
+int fe_last_error(char* buf, size_t n) {
+    if (buf && n) {
+        std::strncpy(buf, g_err, n - 1);
+        buf[n - 1] = '\0';
+    }
+    return FE_OK;
+}
+
+int fe_mesh_create(int32_t nx, int32_t ny, int32_t nz, double hx, double hy, double hz, int32_t p,
+                   int32_t dirichlet, fe_mesh** out) {
+    if (!out) return fail(FE_EINVAL, "fe_mesh_create: out is NULL");
+    *out = nullptr;
+    if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2)
+        return fail(FE_EINVAL, "fe_mesh_create: cells per direction must be even and >= 2 (got %d %d %d)", nx, ny, nz);
+    if (nx > 2046 || ny > 2046 || nz > 2046)
+        return fail(FE_EINVAL, "fe_mesh_create: at most 2046 cells per direction");
+    if (!(hx > 0) || !(hy > 0) || !(hz > 0)) return fail(FE_EINVAL, "fe_mesh_create: cell sizes must be > 0");
+    if (p < 1 || p > 6) return fail(FE_EINVAL, "fe_mesh_create: degree p must be in 1..6 (got %d)", p);
+    if (dirichlet != 0 && dirichlet != 1) return fail(FE_EINVAL, "fe_mesh_create: dirichlet must be 0 or 1");
+    fe_mesh* m = new (std::nothrow) fe_mesh();
+    if (!m) return fail(FE_ENOMEM, "fe_mesh_create: out of host memory");
+    m->nx = nx; m->ny = ny; m->nz = nz; m->p = p; m->dirichlet = dirichlet;
+    m->h[0] = hx; m->h[1] = hy; m->h[2] = hz;
+    m->np[0] = nx / 2; m->np[1] = ny / 2; m->np[2] = nz / 2;
+    m->L[0] = p * nx + 1; m->L[1] = p * ny + 1; m->L[2] = p * nz + 1;
+    m->n_patches = m->np[0] * m->np[1] * m->np[2];
+    try {
+        std::vector<uint64_t> code(m->n_patches);
+        m->rank_to_pid.resize(m->n_patches);
+        for (int id = 0; id < m->n_patches; ++id) {
+            int px, py, pz;
+            m->pxyz(id, px, py, pz);
+            code[id] = spread3(px) | (spread3(py) << 1) | (spread3(pz) << 2);
+            m->rank_to_pid[id] = id;
+        }
+        std::stable_sort(m->rank_to_pid.begin(), m->rank_to_pid.end(),
+                         [&](int a, int b) { return code[a] < code[b]; });
+        m->pid_to_rank.resize(m->n_patches);
+        for (int r = 0; r < m->n_patches; ++r) m->pid_to_rank[m->rank_to_pid[r]] = r;
+        m->rb_ptr.assign(m->n_patches + 1, 0);
+        m->max_rows = 0;
+        for (int r = 0; r < m->n_patches; ++r) {
+            int px, py, pz;
+            m->pxyz(m->rank_to_pid[r], px, py, pz);
+            const int rows = m->rows_of(px, py, pz);
+            m->max_rows = std::max(m->max_rows, rows);
+            m->rb_ptr[r + 1] = m->rb_ptr[r] + rows;
+        }
+        build_consts(*m);
+    } catch (const std::bad_alloc&) {
+        delete m;
+        return fail(FE_ENOMEM, "fe_mesh_create: out of host memory");
+    }
+    *out = m;
+    return FE_OK;
+}
+
+int fe_mesh_destroy(fe_mesh* m) {
+    delete m;
+    return FE_OK;
+}
+
+int fe_mesh_get_info(const fe_mesh* m, fe_mesh_info_t* info) {
+    if (!m || !info) return fail(FE_EINVAL, "fe_mesh_get_info: NULL argument");
+    info->nx = m->nx; info->ny = m->ny; info->nz = m->nz; info->p = m->p;
+    info->dirichlet = m->dirichlet;
+    info->npx = m->np[0]; info->npy = m->np[1]; info->npz = m->np[2];
+    info->lx = m->L[0]; info->ly = m->L[1]; info->lz = m->L[2];
+    info->n_row_blocks = m->n_patches;
+    info->max_rows_per_block = m->max_rows;
+    info->nq1 = m->p + 1;
+    info->n_dofs = (int64_t)m->L[0] * m->L[1] * m->L[2];
+    info->n_cells = (int64_t)m->nx * m->ny * m->nz;
+    info->n_q = info->n_cells * (int64_t)(m->p + 1) * (m->p + 1) * (m->p + 1);
+    info->hx = m->h[0]; info->hy = m->h[1]; info->hz = m->h[2];
+    return FE_OK;
+}
+
+int fe_mesh_row_blocks(const fe_mesh* m, int64_t* rb_ptr) {
+    if (!m || !rb_ptr) return fail(FE_EINVAL, "fe_mesh_row_blocks: NULL argument");
+    std::copy(m->rb_ptr.begin(), m->rb_ptr.end(), rb_ptr);
+    return FE_OK;
+}
+
+int fe_mesh_patch_coords(const fe_mesh* m, int32_t* pxyz) {
+    if (!m || !pxyz) return fail(FE_EINVAL, "fe_mesh_patch_coords: NULL argument");
+    for (int r = 0; r < m->n_patches; ++r) {
+        int px, py, pz;
+        m->pxyz(m->rank_to_pid[r], px, py, pz);
+        pxyz[3 * r] = px; pxyz[3 * r + 1] = py; pxyz[3 * r + 2] = pz;
+    }
+    return FE_OK;
+}
+
+int fe_mesh_dof_keys(const fe_mesh* m, int32_t* ijk) {
+    if (!m || !ijk) return fail(FE_EINVAL, "fe_mesh_dof_keys: NULL argument");
+    const int q = 2 * m->p;
+    for (int r = 0; r < m->n_patches; ++r) {
+        int px, py, pz;
+        m->pxyz(m->rank_to_pid[r], px, py, pz);
+        const int nxq = q + (px == 0), nyq = q + (py == 0), nzq = q + (pz == 0);
+        int64_t d = m->rb_ptr[r];
+        for (int rz = 0; rz < nzq; ++rz)
+            for (int ry = 0; ry < nyq; ++ry)
+                for (int rx = 0; rx < nxq; ++rx, ++d) {
+                    ijk[3 * d] = q * px + rx + (px == 0 ? 0 : 1);
+                    ijk[3 * d + 1] = q * py + ry + (py == 0 ? 0 : 1);
+                    ijk[3 * d + 2] = q * pz + rz + (pz == 0 ? 0 : 1);
+                }
+    }
+    return FE_OK;
+}
+
+int fe_mesh_node_coords(const fe_mesh* m, double* xyz) {
+    if (!m || !xyz) return fail(FE_EINVAL, "fe_mesh_node_coords: NULL argument");
+    const int64_t n = m->rb_ptr.back();
+    std::vector<int32_t> ijk(3 * n);
+    fe_mesh_dof_keys(m, ijk.data());
+    for (int64_t d = 0; d < n; ++d)
+        for (int a = 0; a < 3; ++a) xyz[3 * d + a] = m->coord(a, ijk[3 * d + a]);
+    return FE_OK;
+}
+
+int fe_mesh_quad_points(const fe_mesh* m, double* xyz) {
+    if (!m || !xyz) return fail(FE_EINVAL, "fe_mesh_quad_points: NULL argument");
+    const int n = m->p + 1;
+    int64_t o = 0;
+    for (int r = 0; r < m->n_patches; ++r) {
+        int px, py, pz;
+        m->pxyz(m->rank_to_pid[r], px, py, pz);
+        for (int c = 0; c < 8; ++c) {
+            const int gx = 2 * px + (c & 1), gy = 2 * py + ((c >> 1) & 1), gz = 2 * pz + ((c >> 2) & 1);
+            for (int qz = 0; qz < n; ++qz)
+                for (int qy = 0; qy < n; ++qy)
+                    for (int qx = 0; qx < n; ++qx, ++o) {
+                        xyz[3 * o] = m->h[0] * (gx + m->gx[qx]);
+                        xyz[3 * o + 1] = m->h[1] * (gy + m->gx[qy]);
+                        xyz[3 * o + 2] = m->h[2] * (gz + m->gx[qz]);
+                    }
+        }
+    }
+    return FE_OK;
+}
+
+int fe_mesh_workspace_bytes(const fe_mesh* m, size_t* bytes) {
+    if (!m || !bytes) return fail(FE_EINVAL, "fe_mesh_workspace_bytes: NULL argument");
+    *bytes = 256;
+    return FE_OK;
+}
+
+int fe_mesh_upload(fe_mesh* m, void* ws, size_t bytes, void* stream) {
+    if (!m || !ws) return fail(FE_EINVAL, "fe_mesh_upload: NULL argument");
+    if (bytes < 256) return fail(FE_ENOMEM, "fe_mesh_upload: workspace of %zu bytes is below the 256 needed", bytes);
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(FE_EINVAL, "fe_mesh_upload: workspace must be 256-byte aligned");
+    FE_TRY_CUDA(cudaMemsetAsync(ws, 0, 256, (cudaStream_t)stream), "fe_mesh_upload: cudaMemsetAsync");
+    m->ws = ws;
+    m->ws_bytes = bytes;
+    m->status = reinterpret_cast<int32_t*>(ws);
+    return FE_OK;
+}
+
+int fe_mesh_set_potential(fe_mesh* m, const void* vq, int32_t dtype) {
+    if (!m || !vq) return fail(FE_EINVAL, "fe_mesh_set_potential: NULL argument");
+    if (dtype != FE_F32 && dtype != FE_F64) return fail(FE_EINVAL, "fe_mesh_set_potential: dtype must be FE_F32 or FE_F64");
+    m->vq[dtype == FE_F64] = vq;
+    return FE_OK;
+}
+
+int fe_mesh_check_device(fe_mesh* m, void* stream, int32_t* code) {
+    if (!m || !code) return fail(FE_EINVAL, "fe_mesh_check_device: NULL argument");
+    if (!m->status) return fail(FE_ESTATE, "fe_mesh_check_device: mesh not uploaded");
+    int32_t v = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    FE_TRY_CUDA(cudaMemcpyAsync(&v, m->status, sizeof(v), cudaMemcpyDeviceToHost, s), "fe_mesh_check_device: copy");
+    FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_mesh_check_device: synchronize");
+    *code = v;
+    if (v != 0) {
+        FE_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int32_t), s), "fe_mesh_check_device: reset");
+        return fail(FE_EDEVICE, "device status word = %d", v);
+    }
+    return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 2 and the closed pattern
+// ---------------------------------------------------------------------------
+int fe_column_blocks(const fe_mesh* m, int32_t n_cols, const double* centres, int32_t ncb, int32_t* perm,
+                     int32_t* cbp) {
+    if (!m || !centres || !perm || !cbp) return fail(FE_EINVAL, "fe_column_blocks: NULL argument");
+    if (n_cols < 1 || ncb < 1 || ncb > n_cols) return fail(FE_EINVAL, "fe_column_blocks: need 1 <= n_col_blocks <= n_cols");
+    const int base = n_cols / ncb, rem = n_cols % ncb;
+    if (base + (rem > 0) > kMaxW) return fail(FE_EINVAL, "fe_column_blocks: blocks would be wider than %d", kMaxW);
+    std::vector<int64_t> key(n_cols);
+    const int nc[3] = {m->nx, m->ny, m->nz};
+    for (int j = 0; j < n_cols; ++j) {
+        int g[3];
+        for (int d = 0; d < 3; ++d) {
+            const double v = std::floor(centres[3 * j + d] / m->h[d]);
+            g[d] = v < 0 ? 0 : (v > nc[d] - 1 ? nc[d] - 1 : int(v));
+        }
+        const int r = m->pid_to_rank[m->pid(g[0] / 2, g[1] / 2, g[2] / 2)];
+        key[j] = 8 * (int64_t)r + (g[0] & 1) + 2 * (g[1] & 1) + 4 * (g[2] & 1);
+    }
+    std::vector<int32_t> idx(n_cols);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return key[a] < key[b]; });
+    std::copy(idx.begin(), idx.end(), perm);
+    cbp[0] = 0;
+    for (int c = 0; c < ncb; ++c) cbp[c + 1] = cbp[c] + base + (c < rem ? 1 : 0);
+    return FE_OK;
+}
+
+int fe_pattern_closed(const fe_mesh* m, int32_t ncb, const int64_t* supp_ptr, const int64_t* supp_dofs,
+                      int64_t* row_ptr, int32_t* col_idx, int64_t capacity, int64_t* nnz_out) {
+    if (!m || !supp_ptr || !row_ptr || !nnz_out || ncb < 1) return fail(FE_EINVAL, "fe_pattern_closed: bad argument");
+    const int64_t n_dofs = m->rb_ptr.back();
+    const int64_t n_cells = (int64_t)m->nx * m->ny * m->nz;
+    const int p = m->p;
+    std::vector<uint8_t> pat((size_t)m->n_patches * ncb, 0);
+    std::vector<uint8_t> cellmark(n_cells, 0);
+    std::vector<int64_t> marked;
+    for (int c = 0; c < ncb; ++c) {
+        marked.clear();
+        for (int64_t s = supp_ptr[c]; s < supp_ptr[c + 1]; ++s) {
+            const int64_t dof = supp_dofs[s];
+            if (dof < 0 || dof >= n_dofs) return fail(FE_EINVAL, "fe_pattern_closed: DoF id %lld out of range", (long long)dof);
+            int I, J, K;
+            m->dof_ijk(dof, I, J, K);
+            // cells whose closure holds the node: p*c <= I <= p*(c+1)
+            const int xl = std::max(0, (I + p - 1) / p - 1), xh = std::min(m->nx - 1, I / p);
+            const int yl = std::max(0, (J + p - 1) / p - 1), yh = std::min(m->ny - 1, J / p);
+            const int zl = std::max(0, (K + p - 1) / p - 1), zh = std::min(m->nz - 1, K / p);
+            for (int cz = zl; cz <= zh; ++cz)
+                for (int cy = yl; cy <= yh; ++cy)
+                    for (int cx = xl; cx <= xh; ++cx) {
+                        const int64_t cid = cx + (int64_t)m->nx * (cy + (int64_t)m->ny * cz);
+                        if (!cellmark[cid]) {
+                            cellmark[cid] = 1;
+                            marked.push_back(cid);
+                        }
+                    }
+        }
+        for (int64_t cid : marked) {
+            cellmark[cid] = 0;
+            const int gx = int(cid % m->nx), gy = int((cid / m->nx) % m->ny), gz = int(cid / ((int64_t)m->nx * m->ny));
+            const int px = gx / 2, py = gy / 2, pz = gz / 2;
+            // the cell's nodes lie in its own patch's row block and, along an
+            // axis where the cell is the lower one of its patch, in the lower
+            // neighbour's row block (its index-0 face)
+            for (int dz = 0; dz < 2; ++dz)
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dx = 0; dx < 2; ++dx) {
+                        if (!dx && !((gx & 1) == 0 && px > 0)) continue;
+                        if (!dy && !((gy & 1) == 0 && py > 0)) continue;
+                        if (!dz && !((gz & 1) == 0 && pz > 0)) continue;
+                        const int r = m->pid_to_rank[m->pid(px - 1 + dx, py - 1 + dy, pz - 1 + dz)];
+                        pat[(size_t)r * ncb + c] = 1;
+                    }
+        }
+    }
+    int64_t nnz = 0;
+    row_ptr[0] = 0;
+    for (int r = 0; r < m->n_patches; ++r) {
+        for (int c = 0; c < ncb; ++c) nnz += pat[(size_t)r * ncb + c];
+        row_ptr[r + 1] = nnz;
+    }
+    *nnz_out = nnz;
+    if (capacity < nnz || !col_idx) return fail(FE_ENOMEM, "fe_pattern_closed: capacity %lld below %lld", (long long)capacity, (long long)nnz);
+    int64_t k = 0;
+    for (int r = 0; r < m->n_patches; ++r)
+        for (int c = 0; c < ncb; ++c)
+            if (pat[(size_t)r * ncb + c]) col_idx[k++] = c;
+    return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// BCSR
+// ---------------------------------------------------------------------------
+int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t* cbp, const int64_t* row_ptr,
+                   const int32_t* col_idx, int32_t dtype, fe_bcsr** out) {
+    if (!out) return fail(FE_EINVAL, "fe_bcsr_create: out is NULL");
+    *out = nullptr;
+    if (!m || !cbp || !row_ptr) return fail(FE_EINVAL, "fe_bcsr_create: NULL argument");
+    if (dtype != FE_F32 && dtype != FE_F64) return fail(FE_EINVAL, "fe_bcsr_create: dtype must be FE_F32 or FE_F64");
+    if (n_cols < 1 || ncb < 1) return fail(FE_EINVAL, "fe_bcsr_create: need n_cols >= 1 and n_col_blocks >= 1");
+    if (cbp[0] != 0 || cbp[ncb] != n_cols) return fail(FE_EPATTERN, "fe_bcsr_create: col_block_ptr must run from 0 to n_cols");
+    int wmax = 0;
+    for (int c = 0; c < ncb; ++c) {
+        const int w = cbp[c + 1] - cbp[c];
+        if (w < 1 || w > kMaxW) return fail(FE_EPATTERN, "fe_bcsr_create: column block %d has width %d (allowed 1..%d)", c, w, kMaxW);
+        wmax = std::max(wmax, w);
+    }
+    const int R = m->n_patches;
+    if (row_ptr[0] != 0) return fail(FE_EPATTERN, "fe_bcsr_create: row_ptr[0] must be 0");
+    for (int r = 0; r < R; ++r) {
+        if (row_ptr[r + 1] < row_ptr[r]) return fail(FE_EPATTERN, "fe_bcsr_create: row_ptr decreases at row block %d", r);
+        for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+            if (!col_idx) return fail(FE_EPATTERN, "fe_bcsr_create: col_idx is NULL");
+            if (col_idx[k] < 0 || col_idx[k] >= ncb) return fail(FE_EPATTERN, "fe_bcsr_create: column block %d out of range in row block %d", col_idx[k], r);
+            if (k > row_ptr[r] && col_idx[k] <= col_idx[k - 1])
+                return fail(FE_EPATTERN, "fe_bcsr_create: column blocks of row block %d are not strictly ascending", r);
+        }
+    }
+    if (m->p > kMaxP) return fail(FE_EUNSUPPORTED, "fe_bcsr_create: GPU kernels support p <= %d", kMaxP);
+    fe_bcsr* b = new (std::nothrow) fe_bcsr();
+    if (!b) return fail(FE_ENOMEM, "fe_bcsr_create: out of host memory");
+    try {
+        b->mesh = m;
+        b->n_cols = n_cols; b->ncb = ncb; b->dtype = dtype; b->wmax = wmax;
+        b->cbp.assign(cbp, cbp + ncb + 1);
+        b->row_ptr.assign(row_ptr, row_ptr + R + 1);
+        const int64_t nnz = row_ptr[R];
+        b->col_idx.assign(col_idx, col_idx + nnz);
+        const int64_t align_elems = 16 / (int64_t)b->elem();
+        b->blk_off.resize(nnz);
+        b->dense.assign((size_t)R * ncb, -1);
+        int64_t o = 0;
+        uint64_t fp = hash_mix(0, (uint64_t)ncb);
+        fp = hash_mix(fp, (uint64_t)n_cols);
+        for (int c = 0; c <= ncb; ++c) fp = hash_mix(fp, (uint64_t)cbp[c]);
+        for (int r = 0; r < R; ++r) {
+            const int64_t rows = m->rb_ptr[r + 1] - m->rb_ptr[r];
+            for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+                const int c = b->col_idx[k];
+                const int64_t sz = rows * (cbp[c + 1] - cbp[c]);
+                b->blk_off[k] = o;
+                b->dense[(size_t)r * ncb + c] = k;
+                b->stored += sz;
+                o += (sz + align_elems - 1) / align_elems * align_elems;
+                fp = hash_mix(fp, ((uint64_t)r << 20) ^ (uint64_t)c);
+            }
+        }
+        b->n_values = o;
+        b->fingerprint = fp;
+
+        // ---- apply tiles: for each patch, the union of the column blocks of
+        // the (up to) eight row blocks it touches (Alg. 4/5 semantics) -----
+        std::vector<int> cand;
+        for (int r = 0; r < R; ++r) {
+            int px, py, pz;
+            m->pxyz(m->rank_to_pid[r], px, py, pz);
+            int rb[8];
+            cand.clear();
+            for (int s = 0; s < 8; ++s) {
+                const int qx = px - 1 + (s & 1), qy = py - 1 + ((s >> 1) & 1), qz = pz - 1 + ((s >> 2) & 1);
+                rb[s] = (qx < 0 || qy < 0 || qz < 0) ? -1 : m->pid_to_rank[m->pid(qx, qy, qz)];
+                if (rb[s] >= 0)
+                    for (int64_t k = row_ptr[rb[s]]; k < row_ptr[rb[s] + 1]; ++k) cand.push_back(col_idx[k]);
+            }
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            for (int c : cand) {
+                Tile t;
+                for (int s = 0; s < 8; ++s) {
+                    const int64_t k = rb[s] >= 0 ? b->dense[(size_t)rb[s] * ncb + c] : -1;
+                    t.off[s] = k >= 0 ? b->blk_off[k] : -1;
+                }
+                t.patch = r;
+                t.pxyz = px | (py << 10) | (pz << 20);
+                t.width = cbp[c + 1] - cbp[c];
+                int mask = 0;
+                for (int cell = 0; cell < 8; ++cell) {
+                    const int cx = cell & 1, cy = (cell >> 1) & 1, cz = (cell >> 2) & 1;
+                    bool any = false;
+                    for (int s = 0; s < 8 && !any; ++s) {
+                        const int dx = s & 1, dy = (s >> 1) & 1, dz = (s >> 2) & 1;
+                        if (!dx && cx) continue;
+                        if (!dy && cy) continue;
+                        if (!dz && cz) continue;
+                        any = t.off[s] >= 0;
+                    }
+                    if (any) mask |= 1 << cell;
+                }
+                t.cellmask = mask;
+                b->active_cell_cols += (int64_t)__builtin_popcount(mask) * t.width;
+                b->tiles.push_back(t);
+            }
+        }
+
+        // ---- Gram work lists, grouped by output block (c1, c2) -------------
+        constexpr int kChunk = 16;
+        std::vector<std::vector<GramEntry>> bucket((size_t)ncb * ncb);
+        for (int r = 0; r < R; ++r) {
+            const int32_t rows = int32_t(m->rb_ptr[r + 1] - m->rb_ptr[r]);
+            for (int64_t k1 = row_ptr[r]; k1 < row_ptr[r + 1]; ++k1)
+                for (int64_t k2 = row_ptr[r]; k2 < row_ptr[r + 1]; ++k2) {
+                    const int c1 = col_idx[k1], c2 = col_idx[k2];
+                    bucket[(size_t)c1 * ncb + c2].push_back(GramEntry{b->blk_off[k1], b->blk_off[k2], rows, 0});
+                    b->gram_flops += 2.0 * rows * (cbp[c1 + 1] - cbp[c1]) * (cbp[c2 + 1] - cbp[c2]);
+                }
+        }
+        for (int c1 = 0; c1 < ncb; ++c1)
+            for (int c2 = 0; c2 < ncb; ++c2) {
+                const auto& v = bucket[(size_t)c1 * ncb + c2];
+                for (size_t s = 0; s < v.size(); s += kChunk) {
+                    const int32_t beg = int32_t(b->e_py.size());
+                    const size_t e = std::min(v.size(), s + kChunk);
+                    b->e_py.insert(b->e_py.end(), v.begin() + s, v.begin() + e);
+                    b->i_py.push_back(GramItem{c1, c2, beg, int32_t(b->e_py.size())});
+                    if (c1 <= c2) {
+                        const int32_t beg2 = int32_t(b->e_pp.size());
+                        b->e_pp.insert(b->e_pp.end(), v.begin() + s, v.begin() + e);
+                        b->i_pp.push_back(GramItem{c1, c2, beg2, int32_t(b->e_pp.size())});
+                    }
+                }
+            }
+        size_t off = 0;
+        b->off_tiles = off; off = align_up(off + b->tiles.size() * sizeof(Tile), 256);
+        b->off_epy = off;   off = align_up(off + b->e_py.size() * sizeof(GramEntry), 256);
+        b->off_ipy = off;   off = align_up(off + b->i_py.size() * sizeof(GramItem), 256);
+        b->off_epp = off;   off = align_up(off + b->e_pp.size() * sizeof(GramEntry), 256);
+        b->off_ipp = off;   off = align_up(off + b->i_pp.size() * sizeof(GramItem), 256);
+        b->off_cbp = off;   off = align_up(off + b->cbp.size() * sizeof(int32_t), 256);
+        b->table_bytes = off;
+    } catch (const std::bad_alloc&) {
+        delete b;
+        return fail(FE_ENOMEM, "fe_bcsr_create: out of host memory");
+    }
+    *out = b;
+    return FE_OK;
+}
+
+int fe_bcsr_destroy(fe_bcsr* b) {
+    delete b;
+    return FE_OK;
+}
+
+int fe_bcsr_get_info(const fe_bcsr* b, fe_bcsr_info_t* info) {
+    if (!b || !info) return fail(FE_EINVAL, "fe_bcsr_get_info: NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_cols = b->n_cols;
+    info->n_col_blocks = b->ncb;
+    info->n_row_blocks = b->mesh->n_patches;
+    info->dtype = b->dtype;
+    info->max_width = b->wmax;
+    info->nnz_blocks = (int64_t)b->col_idx.size();
+    info->n_values = b->n_values;
+    info->stored_entries = b->stored;
+    info->value_bytes = (size_t)b->n_values * b->elem();
+    info->table_bytes = b->table_bytes;
+    info->n_tiles = (int64_t)b->tiles.size();
+    info->active_cell_cols = b->active_cell_cols;
+    info->n_gram_items_py = (int64_t)b->i_py.size();
+    info->n_gram_items_pp = (int64_t)b->i_pp.size();
+    info->gram_flops = b->gram_flops;
+    return FE_OK;
+}
+
+int fe_bcsr_block_offsets(const fe_bcsr* b, int64_t* offsets) {
+    if (!b || !offsets) return fail(FE_EINVAL, "fe_bcsr_block_offsets: NULL argument");
+    std::copy(b->blk_off.begin(), b->blk_off.end(), offsets);
+    return FE_OK;
+}
+
+int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
+    if (!b || !values) return fail(FE_EINVAL, "fe_bcsr_bind: NULL argument");
+    if (reinterpret_cast<uintptr_t>(values) % 256 || (tables && reinterpret_cast<uintptr_t>(tables) % 256))
+        return fail(FE_EINVAL, "fe_bcsr_bind: device buffers must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (tables) {
+        char* t = static_cast<char*>(tables);
+        auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+            return bytes ? cudaMemcpyAsync(t + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+        };
+        FE_TRY_CUDA(put(b->off_tiles, b->tiles.data(), b->tiles.size() * sizeof(Tile)), "fe_bcsr_bind: tiles");
+        FE_TRY_CUDA(put(b->off_epy, b->e_py.data(), b->e_py.size() * sizeof(GramEntry)), "fe_bcsr_bind: gram entries");
+        FE_TRY_CUDA(put(b->off_ipy, b->i_py.data(), b->i_py.size() * sizeof(GramItem)), "fe_bcsr_bind: gram items");
+        FE_TRY_CUDA(put(b->off_epp, b->e_pp.data(), b->e_pp.size() * sizeof(GramEntry)), "fe_bcsr_bind: gram entries");
+        FE_TRY_CUDA(put(b->off_ipp, b->i_pp.data(), b->i_pp.size() * sizeof(GramItem)), "fe_bcsr_bind: gram items");
+        FE_TRY_CUDA(put(b->off_cbp, b->cbp.data(), b->cbp.size() * sizeof(int32_t)), "fe_bcsr_bind: column blocks");
+        // the source arrays are members of the handle; make sure the copies
+        // are done before a later re-bind could free them
+        FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_bcsr_bind: synchronize");
+    }
+    b->values = values;
+    b->tables = tables;
+    return FE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Hot path
+// ---------------------------------------------------------------------------
+namespace {
+
+int check_pair(const char* fn, const fe_mesh* m, const fe_bcsr* P, const fe_bcsr* Y) {
+    if (!P || !Y) return fail(FE_EINVAL, "%s: NULL multivector", fn);
+    if (m && (P->mesh != m || Y->mesh != m)) return fail(FE_EINVAL, "%s: multivectors belong to another mesh", fn);
+    if (P->dtype != Y->dtype) return fail(FE_EPATTERN, "%s: P and Y have different dtypes", fn);
+    if (P->fingerprint != Y->fingerprint || P->col_idx != Y->col_idx || P->cbp != Y->cbp)
+        return fail(FE_EPATTERN, "%s: P and Y must have identical block patterns and column blocks", fn);
+    if (!P->values || !P->tables) return fail(FE_ESTATE, "%s: P is not bound with values and tables", fn);
+    if (!Y->values) return fail(FE_ESTATE, "%s: Y is not bound", fn);
+    return FE_OK;
+}
+
+int choose_cells_per_round(int p, int wmax, int dtype, int& cpr) {
+    const int candidates[4] = {8, 4, 2, 1};
+    for (int c : candidates) {
+        const size_t smem = dtype == FE_F64 ? apply_smem_bytes<double>(p, wmax, c) : apply_smem_bytes<float>(p, wmax, c);
+        const int thr = apply_threads<float>(p, wmax, c);
+        if (smem <= 227 * 1024 && thr <= apply_max_threads(p)) {
+            cpr = c;
+            return FE_OK;
+        }
+    }
+    return fail(FE_EUNSUPPORTED, "apply: no launch shape fits p=%d width=%d", p, wmax);
+}
+
+template <typename T>
+int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s) {
+    ApplyArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.P = static_cast<const T*>(P->values);
+    a.Y = static_cast<T*>(Y->values);
+    a.Vq = static_cast<const T*>(m->vq[sizeof(T) == 8]);
+    a.tiles = reinterpret_cast<const Tile*>(static_cast<const char*>(P->tables) + P->off_tiles);
+    a.n_tiles = (int64_t)P->tiles.size();
+    a.npx = m->np[0]; a.npy = m->np[1]; a.npz = m->np[2];
+    a.lx = m->L[0]; a.ly = m->L[1]; a.lz = m->L[2];
+    a.dirichlet = m->dirichlet;
+    a.wmax = P->wmax;
+    int cpr = 8;
+    int rc = choose_cells_per_round(m->p, P->wmax, P->dtype, cpr);
+    if (rc) return rc;
+    a.cells_per_round = cpr;
+    a.status = m->status;
+    if constexpr (sizeof(T) == 8) a.k = m->kd; else a.k = m->kf;
+    FE_TRY_CUDA(cudaMemsetAsync(Y->values, 0, (size_t)Y->n_values * sizeof(T), s), "fe_apply_H: zero Y");
+    FE_TRY_CUDA(launch_apply<T>(m->p, a, s), "fe_apply_H: kernel launch");
+    return FE_OK;
+}
+
+template <typename T>
+int gram_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaStream_t s) {
+    GramArgs<T> g;
+    const char* t = static_cast<const char*>(A->tables);
+    g.A = static_cast<const T*>(A->values);
+    g.B = static_cast<const T*>(B->values);
+    g.entries = reinterpret_cast<const GramEntry*>(t + (sym ? A->off_epp : A->off_epy));
+    g.items = reinterpret_cast<const GramItem*>(t + (sym ? A->off_ipp : A->off_ipy));
+    g.n_items = (int64_t)(sym ? A->i_pp.size() : A->i_py.size());
+    g.cb_ptr = reinterpret_cast<const int32_t*>(t + A->off_cbp);
+    g.n_cols = A->n_cols;
+    g.symmetric = sym ? 1 : 0;
+    g.G = G;
+    FE_TRY_CUDA(cudaMemsetAsync(G, 0, (size_t)A->n_cols * A->n_cols * sizeof(double), s), "gram: zero G");
+    FE_TRY_CUDA(launch_gram<T>(g, s), "gram: kernel launch");
+    return FE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_apply_H(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, void* stream) {
+    if (!m) return fail(FE_EINVAL, "fe_apply_H: mesh is NULL");
+    int rc = check_pair("fe_apply_H", m, P, Y);
+    if (rc) return rc;
+    if (!m->status) return fail(FE_ESTATE, "fe_apply_H: mesh is not uploaded");
+    if (!m->vq[P->dtype == FE_F64]) return fail(FE_ESTATE, "fe_apply_H: no potential of this dtype registered");
+    if (m->p > kMaxP) return fail(FE_EUNSUPPORTED, "fe_apply_H: GPU kernels support p <= %d", kMaxP);
+    cudaStream_t s = (cudaStream_t)stream;
+    return P->dtype == FE_F64 ? apply_impl<double>(m, P, Y, s) : apply_impl<float>(m, P, Y, s);
+}
+
+int fe_gram_PtY(const fe_bcsr* P, const fe_bcsr* Y, double* G, void* stream) {
+    int rc = check_pair("fe_gram_PtY", nullptr, P, Y);
+    if (rc) return rc;
+    if (!G) return fail(FE_EINVAL, "fe_gram_PtY: G is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    return P->dtype == FE_F64 ? gram_impl<double>(P, Y, false, G, s) : gram_impl<float>(P, Y, false, G, s);
+}
+
+int fe_gram_PtP(const fe_bcsr* P, double* G, void* stream) {
+    if (!P || !G) return fail(FE_EINVAL, "fe_gram_PtP: NULL argument");
+    if (!P->values || !P->tables) return fail(FE_ESTATE, "fe_gram_PtP: P is not bound with values and tables");
+    cudaStream_t s = (cudaStream_t)stream;
+    return P->dtype == FE_F64 ? gram_impl<double>(P, P, true, G, s) : gram_impl<float>(P, P, true, G, s);
+}
+
+int fe_apply_H_gram(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY, double* G_PP, void* stream) {
+    int rc = fe_apply_H(m, P, Y, stream);
+    if (rc) return rc;
+    rc = fe_gram_PtY(P, Y, G_PY, stream);
+    if (rc) return rc;
+    return fe_gram_PtP(P, G_PP, stream);
+}
+
+int fe_apply_H_gram_host(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY, double* G_PP, const void* P_host,
+                         void* Y_host, double* G_PY_host, double* G_PP_host, void* stream) {
+    if (!P_host || !Y_host || !G_PY_host || !G_PP_host) return fail(FE_EINVAL, "fe_apply_H_gram_host: NULL host buffer");
+    int rc = check_pair("fe_apply_H_gram_host", m, P, Y);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = (size_t)P->n_values * P->elem();
+    const size_t gb = (size_t)P->n_cols * P->n_cols * sizeof(double);
+    FE_TRY_CUDA(cudaMemcpyAsync(P->values, P_host, vb, cudaMemcpyHostToDevice, s), "fe_apply_H_gram_host: copy P in");
+    rc = fe_apply_H_gram(m, P, Y, G_PY, G_PP, stream);
+    if (rc) return rc;
+    FE_TRY_CUDA(cudaMemcpyAsync(Y_host, Y->values, vb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy Y out");
+    FE_TRY_CUDA(cudaMemcpyAsync(G_PY_host, G_PY, gb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy G_PY out");
+    FE_TRY_CUDA(cudaMemcpyAsync(G_PP_host, G_PP, gb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy G_PP out");
+    FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_apply_H_gram_host: synchronize");
+    return FE_OK;
+}
+
+int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream) {
+    if (!flops_per_s || iters < 1 || (dtype != FE_F32 && dtype != FE_F64))
+        return fail(FE_EINVAL, "fe_probe_fma: bad argument");
+    FE_TRY_CUDA(probe_fma(dtype, iters, flops_per_s, (cudaStream_t)stream), "fe_probe_fma");
+    return FE_OK;
+}
+
+}  // extern "C"

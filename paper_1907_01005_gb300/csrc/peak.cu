@@ -1,0 +1,60 @@
+// FMA throughput probe: the FP32 / FP64 ALU peaks that the roofline of the
+// cell kernels and of the FP64 Gram is reported against.  Each thread runs
+// eight independent FMA chains so that latency is hidden; the grid covers
+// every SM several times.
+#include "fe_internal.h"
+
+namespace femf {
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_chains(T* out, int64_t iters, T a, T b) {
+    T x0 = T(threadIdx.x), x1 = x0 + T(1), x2 = x0 + T(2), x3 = x0 + T(3);
+    T x4 = x0 + T(4), x5 = x0 + T(5), x6 = x0 + T(6), x7 = x0 + T(7);
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+            x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+        }
+    }
+    const T s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+    if (s == T(-1.2345)) out[blockIdx.x] = s;   // keeps the chains alive
+}
+
+}  // namespace
+
+cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * 8, threads = 256;
+    void* out = nullptr;
+    e = cudaMallocAsync(&out, sizeof(double) * blocks, s);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    for (int rep = 0; rep < 2; ++rep) {   // first pass warms up the clocks
+        cudaEventRecord(t0, s);
+        if (dtype == FE_F64)
+            fma_chains<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.999999, 1e-7);
+        else
+            fma_chains<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-7f);
+        cudaEventRecord(t1, s);
+    }
+    e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaFreeAsync(out, s);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * 8 * 16 * (double)iters * blocks * threads;
+    *flops_per_s = flops / (ms * 1e-3);
+    return cudaGetLastError();
+}
+
+}  // namespace femf
