@@ -165,7 +165,7 @@ typedef struct {
     int32_t pad_;
     int64_t nnz_blocks;           /* stored (row block, column block) blocks */
     int64_t n_values;             /* value slots, padding included */
-    int64_t stored_entries;       /* sum over blocks of rows*width */
+    int64_t stored_entries;       /* sum over blocks of rows*width (padding excluded) */
     size_t value_bytes;           /* bytes of the value array */
     size_t table_bytes;           /* bytes of the device tables (tiles, Gram lists) */
     int64_t n_tiles;              /* (patch, column block) work items of the apply */
@@ -180,9 +180,13 @@ typedef struct {
  * row_ptr[n_row_blocks+1] / col_idx[nnz] (strictly ascending per row block,
  * in range; FE_EPATTERN otherwise).  dtype: FE_F32 or FE_F64.
  * Value layout: the blocks are stored one after another in CSR order; block
- * (r, c) holds rows_r x w_c values row-major (row = DoF of the row block in
- * its local order, column = column inside the block), and starts at an
- * element offset that is a multiple of 16 bytes (fe_bcsr_block_offsets). */
+ * (r, c) holds rows_r rows (the DoFs of the row block in its local order) of
+ * ld_c values each, row-major, where ld_c is the width w_c rounded up to a
+ * multiple of 16 bytes (fe_bcsr_row_strides) so that every row starts on a
+ * 16-byte boundary (the paper pads rows to a cache line, Sec. 3.5, for the
+ * same reason: aligned vector access).  Entry (row, j) of the block, j < w_c,
+ * is column col_block_ptr[c] + j.  Padding entries are ignored on input and
+ * left zero on output.  Blocks start at the offsets of fe_bcsr_block_offsets. */
 int fe_bcsr_create(const fe_mesh* mesh, int32_t n_cols, int32_t n_col_blocks,
                    const int32_t* col_block_ptr, const int64_t* row_ptr, const int32_t* col_idx,
                    int32_t dtype, fe_bcsr** out);
@@ -192,6 +196,9 @@ int fe_bcsr_get_info(const fe_bcsr* bcsr, fe_bcsr_info_t* info);
 /* offsets[nnz_blocks]: element offset of the first value of each block, in
  * CSR order. */
 int fe_bcsr_block_offsets(const fe_bcsr* bcsr, int64_t* offsets);
+
+/* ld[n_col_blocks]: row stride (elements) of the blocks of each column block. */
+int fe_bcsr_row_strides(const fe_bcsr* bcsr, int32_t* ld);
 
 /* Attaches the caller's device value array (value_bytes, 256-byte aligned)
  * and, when the multivector is used as the source P of fe_apply_H /
@@ -240,9 +247,10 @@ int fe_apply_H_gram_host(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_
  * Measurement helper (not part of the paper's method)
  * ------------------------------------------------------------------------ */
 
-/* Runs an FMA-throughput probe of the given dtype on the current device
- * (eight independent FMA chains per thread, 8 CTAs of 256 threads per SM,
- * `iters` x 128 FMAs per chain) and returns the achieved flop/s (2 per FMA),
+/* Runs an FMA-throughput probe on the current device (dtype FE_F32, FE_F64,
+ * or 3 for packed FP32x2 FMA; eight independent chains per thread, 8 CTAs of
+ * 256 threads per SM, `iters` x 128 FMAs per thread) and returns the achieved
+ * flop/s (2 per FMA),
  * the ALU peak used for the roofline of ALU-bound kernels.  Synchronises
  * `stream`; uses a small stream-ordered allocation. */
 int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream);

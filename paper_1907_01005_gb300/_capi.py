@@ -77,6 +77,7 @@ SIGNATURES = {
     "fe_bcsr_destroy": [_P],
     "fe_bcsr_get_info": [_P, C.POINTER(fe_bcsr_info_t)],
     "fe_bcsr_block_offsets": [_P, _P],
+    "fe_bcsr_row_strides": [_P, _P],
     "fe_bcsr_bind": [_P, _P, _P, _P],
     "fe_apply_H": [_P, _P, _P, _P],
     "fe_gram_PtY": [_P, _P, _P, _P],

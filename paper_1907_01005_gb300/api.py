@@ -163,6 +163,11 @@ class BCSR:
         check(capi.fe_bcsr_block_offsets(self.h, _hptr(a)))
         return a[: int(self.info.nnz_blocks)]
 
+    def row_strides(self) -> np.ndarray:
+        a = np.empty(len(self.cbp) - 1, np.int32)
+        check(capi.fe_bcsr_row_strides(self.h, _hptr(a)))
+        return a
+
     def alloc(self, device="cuda", with_tables=True):
         import torch
         vals = torch.zeros(int(self.info.n_values), dtype=torch_dtype(self.dtype), device=device)

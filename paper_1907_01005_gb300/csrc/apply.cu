@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
     T* exB = exA + cpr * wmax * N3;
 
     const Tile& tile = a.tiles[blockIdx.x];
-    const int w = tile.width;
+    const int w = tile.width, ld = tile.ld;
     const int px = tile.pxyz & 1023, py = (tile.pxyz >> 10) & 1023, pz = tile.pxyz >> 20;
     const int cellmask = tile.cellmask;
     if (w > wmax || w < 1) {
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
             node_slot_row<P>(i, j, k, px, py, pz, slot, row);
             const bool bnd = a.dirichlet &&
                 on_boundary(2 * P * px + i, 2 * P * py + j, 2 * P * pz + k, a.lx, a.ly, a.lz);
-            if (off[slot] >= 0 && !bnd) v = a.P[off[slot] + (int64_t)row * w + col];
+            if (off[slot] >= 0 && !bnd) v = a.P[off[slot] + (int64_t)row * ld + col];
         }
         U[e] = v;
         Yp[e] = T(0);
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
         node_slot_row<P>(i, j, k, px, py, pz, slot, row);
         const bool bnd = a.dirichlet &&
             on_boundary(2 * P * px + i, 2 * P * py + j, 2 * P * pz + k, a.lx, a.ly, a.lz);
-        if (off[slot] >= 0 && !bnd) atomicAdd(&a.Y[off[slot] + (int64_t)row * w + c], Yp[e]);
+        if (off[slot] >= 0 && !bnd) atomicAdd(&a.Y[off[slot] + (int64_t)row * ld + c], Yp[e]);
     }
 }
 

@@ -32,6 +32,10 @@ struct CellConsts {
     T Sb[kMaxN][kMaxN];
     T A[3][kMaxN][kMaxN];
     T jxw;       // |J| = hx hy hz
+    // Variant used by the register-resident kernel, which takes V unscaled:
+    // A / |J| in A above and |J| Sb here, for the first of the three
+    // transposed interpolations only (the other two use Sb).
+    T Sb1[kMaxN][kMaxN];
 };
 
 // One (patch, column block) work item of the apply.  Slot b = dx + 2 dy + 4 dz
@@ -44,6 +48,26 @@ struct Tile {
     int32_t pxyz;       // px | py << 10 | pz << 20
     int32_t width;      // column block width
     int32_t cellmask;   // bit c (c = cx + 2 cy + 4 cz) set iff that cell touches a stored block
+    int32_t ld;         // row stride of the column block's blocks (elements)
+    int32_t pad;
+};
+
+// Packed work unit of the register-resident apply (p <= 2): one patch and up
+// to four of its column blocks with at most 32 columns in total; CTA lane j
+// takes column j of the concatenated blocks.  off[b][s] is the offset of
+// block (row block of slot s, column block b) in units of 16 bytes, or -1.
+constexpr int kUnitBlocks = 4;
+constexpr int kUnitLanes = 32;
+constexpr int kUnitLdSum = 36;    // sum of the blocks' row strides in a unit
+struct Unit {
+    int32_t off[kUnitBlocks][8];
+    int32_t patch;      // rank of the patch
+    int32_t pxyz;       // px | py << 10 | pz << 20
+    int32_t nb;         // column blocks in the unit
+    int32_t width[kUnitBlocks];
+    int32_t ld[kUnitBlocks];
+    int32_t cellmask[kUnitBlocks];
+    int32_t pad;
 };
 
 // Gram work: entries are (block of A, block of B, rows) for one column-block
@@ -58,6 +82,40 @@ struct GramItem {
     int32_t c1, c2;
     int32_t begin, end;
 };
+
+// Tensor-core Gram of FP32 multivectors (gram_tc.cu): work is grouped by
+// runs of consecutive row blocks; a group's union of column blocks is laid
+// out as `width` dense columns, and its output is tiled 32 x 32.
+constexpr int kMaxGroup = 8;     // row blocks per group
+constexpr int kMaxUnion = 64;    // column blocks in a group's union
+struct GramTcGroup {
+    int32_t r0, r1;     // row blocks [r0, r1)
+    int32_t k_rows;     // rows of the group
+    int32_t n_u;        // column blocks in the union
+    int32_t width;      // columns of the union
+    int32_t u_base;     // offset of the group's (r1-r0) x n_u block-offset table
+    int32_t c_base;     // offset of the group's column tables
+    int32_t pad;
+};
+struct GramTcItem {
+    int32_t group;
+    int32_t tile;       // mi | ni << 16 (square tiles of gram_tc_tile() union columns)
+};
+struct GramTcArgs {
+    const float* A;
+    const float* B;
+    const GramTcGroup* groups;
+    const GramTcItem* items;
+    int64_t n_items;
+    const int64_t* union_off;   // element offset of block (row block, union slot) or -1
+    const int32_t* col_info;    // (slot << 16) | (column in block << 8) | row stride of the block
+    const int32_t* col_glob;    // global column id
+    const int32_t* rows;        // rows of each row block
+    int32_t n_cols;
+    double* G;
+};
+cudaError_t launch_gram_tc(const GramTcArgs& a, bool symmetric, cudaStream_t s);
+int gram_tc_tile();   // output tile edge of the tensor-core Gram
 
 template <typename T>
 struct ApplyArgs {
@@ -83,6 +141,7 @@ struct GramArgs {
     const GramItem* items;
     int64_t n_items;
     const int32_t* cb_ptr;
+    const int32_t* ld;        // row stride of each column block
     int32_t n_cols;
     int32_t symmetric;        // 1: also write the mirrored block for c1 != c2
     double* G;
@@ -92,6 +151,20 @@ struct GramArgs {
 // message to the caller.
 template <typename T>
 cudaError_t launch_apply(int p, const ApplyArgs<T>& a, cudaStream_t s);
+template <typename T>
+struct ApplyUnitArgs {
+    const T* P;
+    T* Y;
+    const T* Vq;
+    const Unit* units;
+    int64_t n_units;
+    int32_t lx, ly, lz;
+    int32_t dirichlet;
+    int32_t* status;
+    CellConsts<T> k;
+};
+template <typename T>
+cudaError_t launch_apply_units(int p, const ApplyUnitArgs<T>& a, cudaStream_t s);
 template <typename T>
 size_t apply_smem_bytes(int p, int wmax, int cells_per_round);
 template <typename T>

@@ -18,13 +18,14 @@ __global__ void __launch_bounds__(256) gram_pairs_kernel(const GramArgs<T> g) {
     const int w1 = g.cb_ptr[c1 + 1] - col1, w2 = g.cb_ptr[c2 + 1] - col2;
     const int a = threadIdx.x / kMaxW, b = threadIdx.x % kMaxW;
     if (a >= w1 || b >= w2) return;
+    const int ld1 = g.ld[c1], ld2 = g.ld[c2];
     double acc = 0.0;
     for (int e = it.begin; e < it.end; ++e) {
         const GramEntry en = g.entries[e];
         const T* pa = g.A + en.offA + a;
         const T* pb = g.B + en.offB + b;
         for (int r = 0; r < en.rows; ++r)
-            acc = fma(static_cast<double>(pa[(int64_t)r * w1]), static_cast<double>(pb[(int64_t)r * w2]), acc);
+            acc = fma(static_cast<double>(pa[(int64_t)r * ld1]), static_cast<double>(pb[(int64_t)r * ld2]), acc);
     }
     atomicAdd(&g.G[(int64_t)(col1 + a) * g.n_cols + col2 + b], acc);
     if (g.symmetric && c1 != c2) atomicAdd(&g.G[(int64_t)(col2 + b) * g.n_cols + col1 + a], acc);

@@ -172,15 +172,24 @@ struct fe_bcsr {
     const fe_mesh* mesh = nullptr;
     int32_t n_cols = 0, ncb = 0, dtype = 0, wmax = 0;
     std::vector<int32_t> cbp;
+    std::vector<int32_t> ld;             // row stride of each column block (width rounded up to 16 bytes)
     std::vector<int64_t> row_ptr;
     std::vector<int32_t> col_idx;
     std::vector<int64_t> blk_off;
     std::vector<int64_t> dense;          // [r * ncb + c] -> block index or -1
     int64_t n_values = 0, stored = 0;
     std::vector<Tile> tiles;
+    std::vector<Unit> units;          // packed apply work (p <= 2)
     std::vector<GramEntry> e_py, e_pp;
     std::vector<GramItem> i_py, i_pp;
+    // tensor-core Gram (FE_F32)
+    std::vector<GramTcGroup> tc_groups;
+    std::vector<GramTcItem> tc_py, tc_pp;
+    std::vector<int64_t> tc_uoff;
+    std::vector<int32_t> tc_cinfo, tc_cglob, tc_rows;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
+    size_t off_tcg = 0, off_tcpy = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
+    size_t off_units = 0, off_ld = 0;
     int64_t active_cell_cols = 0;
     double gram_flops = 0.0;
     uint64_t fingerprint = 0;
@@ -563,16 +572,25 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         }
     }
     if (m->p > kMaxP) return fail(FE_EUNSUPPORTED, "fe_bcsr_create: GPU kernels support p <= %d", kMaxP);
+    if (dtype == FE_F32)
+        for (int r = 0; r < R; ++r)
+            if (row_ptr[r + 1] - row_ptr[r] > kMaxUnion)
+                return fail(FE_EUNSUPPORTED, "fe_bcsr_create: row block %d holds %lld column blocks; the FP32 Gram supports at most %d",
+                            r, (long long)(row_ptr[r + 1] - row_ptr[r]), kMaxUnion);
     fe_bcsr* b = new (std::nothrow) fe_bcsr();
     if (!b) return fail(FE_ENOMEM, "fe_bcsr_create: out of host memory");
     try {
         b->mesh = m;
         b->n_cols = n_cols; b->ncb = ncb; b->dtype = dtype; b->wmax = wmax;
         b->cbp.assign(cbp, cbp + ncb + 1);
+        b->ld.resize(ncb);
+        for (int cc = 0; cc < ncb; ++cc) {
+            const int w = cbp[cc + 1] - cbp[cc], per16 = 16 / (int)b->elem();
+            b->ld[cc] = (w + per16 - 1) / per16 * per16;
+        }
         b->row_ptr.assign(row_ptr, row_ptr + R + 1);
         const int64_t nnz = row_ptr[R];
         b->col_idx.assign(col_idx, col_idx + nnz);
-        const int64_t align_elems = 16 / (int64_t)b->elem();
         b->blk_off.resize(nnz);
         b->dense.assign((size_t)R * ncb, -1);
         int64_t o = 0;
@@ -583,11 +601,10 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
             const int64_t rows = m->rb_ptr[r + 1] - m->rb_ptr[r];
             for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
                 const int c = b->col_idx[k];
-                const int64_t sz = rows * (cbp[c + 1] - cbp[c]);
                 b->blk_off[k] = o;
                 b->dense[(size_t)r * ncb + c] = k;
-                b->stored += sz;
-                o += (sz + align_elems - 1) / align_elems * align_elems;
+                b->stored += rows * (cbp[c + 1] - cbp[c]);
+                o += rows * b->ld[c];   // a multiple of 16 bytes
                 fp = hash_mix(fp, ((uint64_t)r << 20) ^ (uint64_t)c);
             }
         }
@@ -619,6 +636,7 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                 t.patch = r;
                 t.pxyz = px | (py << 10) | (pz << 20);
                 t.width = cbp[c + 1] - cbp[c];
+                t.ld = b->ld[c];
                 int mask = 0;
                 for (int cell = 0; cell < 8; ++cell) {
                     const int cx = cell & 1, cy = (cell >> 1) & 1, cz = (cell >> 2) & 1;
@@ -636,7 +654,36 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                 b->active_cell_cols += (int64_t)__builtin_popcount(mask) * t.width;
                 b->tiles.push_back(t);
             }
+            // pack this patch's tiles into units of <= 4 blocks and <= 32 columns
+            const size_t first = b->tiles.size() - cand.size();
+            Unit u{};
+            int lanes = 0;
+            auto flush = [&]() {
+                if (u.nb > 0) b->units.push_back(u);
+                u = Unit{};
+                lanes = 0;
+            };
+            int lds = 0;
+            for (size_t ti = first; ti < b->tiles.size(); ++ti) {
+                const Tile& t = b->tiles[ti];
+                if (u.nb == kUnitBlocks || lanes + t.width > kUnitLanes || lds + t.ld > kUnitLdSum) {
+                    flush();
+                    lds = 0;
+                }
+                u.patch = t.patch;
+                u.pxyz = t.pxyz;
+                for (int s = 0; s < 8; ++s) u.off[u.nb][s] = t.off[s] >= 0 ? int32_t(t.off[s] * (int64_t)b->elem() / 16) : -1;
+                u.width[u.nb] = t.width;
+                u.ld[u.nb] = t.ld;
+                u.cellmask[u.nb] = t.cellmask;
+                u.nb += 1;
+                lanes += t.width;
+                lds += t.ld;
+            }
+            flush();
         }
+        if ((int64_t)b->n_values * (int64_t)b->elem() / 16 >= (int64_t)INT32_MAX)
+            throw std::bad_alloc();   // offsets in 16-byte units must fit in int32
 
         // ---- Gram work lists, grouped by output block (c1, c2) -------------
         constexpr int kChunk = 16;
@@ -665,6 +712,57 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                     }
                 }
             }
+        if (dtype == FE_F32) {
+            // ---- tensor-core Gram: groups of consecutive row blocks ----------
+            for (int r = 0; r < m->n_patches;) {
+                GramTcGroup gr{};
+                gr.r0 = r;
+                std::vector<int32_t> uni;
+                int r1 = r;
+                while (r1 < R && r1 - r < kMaxGroup) {
+                    std::vector<int32_t> cand(uni);
+                    cand.insert(cand.end(), col_idx + row_ptr[r1], col_idx + row_ptr[r1 + 1]);
+                    std::sort(cand.begin(), cand.end());
+                    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+                    if ((int)cand.size() > kMaxUnion && r1 > r) break;
+                    uni.swap(cand);
+                    ++r1;
+                }
+                gr.r1 = r1;
+                gr.n_u = (int)uni.size();
+                gr.k_rows = int32_t(m->rb_ptr[r1] - m->rb_ptr[r]);
+                gr.u_base = int32_t(b->tc_uoff.size());
+                gr.c_base = int32_t(b->tc_cinfo.size());
+                int width = 0;
+                for (int rr = r; rr < r1; ++rr)
+                    for (int u = 0; u < gr.n_u; ++u) {
+                        const int64_t k = b->dense[(size_t)rr * ncb + uni[u]];
+                        b->tc_uoff.push_back(k >= 0 ? b->blk_off[k] : -1);
+                    }
+                for (int u = 0; u < gr.n_u; ++u) {
+                    const int w = cbp[uni[u] + 1] - cbp[uni[u]];
+                    for (int a = 0; a < w; ++a) {
+                        b->tc_cinfo.push_back((u << 16) | (a << 8) | b->ld[uni[u]]);
+                        b->tc_cglob.push_back(cbp[uni[u]] + a);
+                    }
+                    width += w;
+                }
+                gr.width = width;
+                if (width > 0) {
+                    const int gidx = (int)b->tc_groups.size();
+                    const int nt = (width + gram_tc_tile() - 1) / gram_tc_tile();
+                    for (int mi = 0; mi < nt; ++mi)
+                        for (int ni = 0; ni < nt; ++ni) {
+                            b->tc_py.push_back(GramTcItem{gidx, mi | (ni << 16)});
+                            if (mi <= ni) b->tc_pp.push_back(GramTcItem{gidx, mi | (ni << 16)});
+                        }
+                    b->tc_groups.push_back(gr);
+                }
+                r = r1;
+            }
+            b->tc_rows.resize(R);
+            for (int rr = 0; rr < R; ++rr) b->tc_rows[rr] = int32_t(m->rb_ptr[rr + 1] - m->rb_ptr[rr]);
+        }
         size_t off = 0;
         b->off_tiles = off; off = align_up(off + b->tiles.size() * sizeof(Tile), 256);
         b->off_epy = off;   off = align_up(off + b->e_py.size() * sizeof(GramEntry), 256);
@@ -672,6 +770,15 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_epp = off;   off = align_up(off + b->e_pp.size() * sizeof(GramEntry), 256);
         b->off_ipp = off;   off = align_up(off + b->i_pp.size() * sizeof(GramItem), 256);
         b->off_cbp = off;   off = align_up(off + b->cbp.size() * sizeof(int32_t), 256);
+        b->off_ld = off;    off = align_up(off + b->ld.size() * sizeof(int32_t), 256);
+        b->off_tcg = off;   off = align_up(off + b->tc_groups.size() * sizeof(GramTcGroup), 256);
+        b->off_tcpy = off;  off = align_up(off + b->tc_py.size() * sizeof(GramTcItem), 256);
+        b->off_tcpp = off;  off = align_up(off + b->tc_pp.size() * sizeof(GramTcItem), 256);
+        b->off_tcu = off;   off = align_up(off + b->tc_uoff.size() * sizeof(int64_t), 256);
+        b->off_tcci = off;  off = align_up(off + b->tc_cinfo.size() * sizeof(int32_t), 256);
+        b->off_tccg = off;  off = align_up(off + b->tc_cglob.size() * sizeof(int32_t), 256);
+        b->off_tcrows = off; off = align_up(off + b->tc_rows.size() * sizeof(int32_t), 256);
+        b->off_units = off; off = align_up(off + b->units.size() * sizeof(Unit), 256);
         b->table_bytes = off;
     } catch (const std::bad_alloc&) {
         delete b;
@@ -713,6 +820,12 @@ int fe_bcsr_block_offsets(const fe_bcsr* b, int64_t* offsets) {
     return FE_OK;
 }
 
+int fe_bcsr_row_strides(const fe_bcsr* b, int32_t* ld) {
+    if (!b || !ld) return fail(FE_EINVAL, "fe_bcsr_row_strides: NULL argument");
+    std::copy(b->ld.begin(), b->ld.end(), ld);
+    return FE_OK;
+}
+
 int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
     if (!b || !values) return fail(FE_EINVAL, "fe_bcsr_bind: NULL argument");
     if (reinterpret_cast<uintptr_t>(values) % 256 || (tables && reinterpret_cast<uintptr_t>(tables) % 256))
@@ -729,6 +842,15 @@ int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
         FE_TRY_CUDA(put(b->off_epp, b->e_pp.data(), b->e_pp.size() * sizeof(GramEntry)), "fe_bcsr_bind: gram entries");
         FE_TRY_CUDA(put(b->off_ipp, b->i_pp.data(), b->i_pp.size() * sizeof(GramItem)), "fe_bcsr_bind: gram items");
         FE_TRY_CUDA(put(b->off_cbp, b->cbp.data(), b->cbp.size() * sizeof(int32_t)), "fe_bcsr_bind: column blocks");
+        FE_TRY_CUDA(put(b->off_ld, b->ld.data(), b->ld.size() * sizeof(int32_t)), "fe_bcsr_bind: row strides");
+        FE_TRY_CUDA(put(b->off_tcg, b->tc_groups.data(), b->tc_groups.size() * sizeof(GramTcGroup)), "fe_bcsr_bind: groups");
+        FE_TRY_CUDA(put(b->off_tcpy, b->tc_py.data(), b->tc_py.size() * sizeof(GramTcItem)), "fe_bcsr_bind: tc items");
+        FE_TRY_CUDA(put(b->off_tcpp, b->tc_pp.data(), b->tc_pp.size() * sizeof(GramTcItem)), "fe_bcsr_bind: tc items");
+        FE_TRY_CUDA(put(b->off_tcu, b->tc_uoff.data(), b->tc_uoff.size() * sizeof(int64_t)), "fe_bcsr_bind: union offsets");
+        FE_TRY_CUDA(put(b->off_tcci, b->tc_cinfo.data(), b->tc_cinfo.size() * sizeof(int32_t)), "fe_bcsr_bind: column info");
+        FE_TRY_CUDA(put(b->off_tccg, b->tc_cglob.data(), b->tc_cglob.size() * sizeof(int32_t)), "fe_bcsr_bind: column ids");
+        FE_TRY_CUDA(put(b->off_tcrows, b->tc_rows.data(), b->tc_rows.size() * sizeof(int32_t)), "fe_bcsr_bind: rows");
+        FE_TRY_CUDA(put(b->off_units, b->units.data(), b->units.size() * sizeof(Unit)), "fe_bcsr_bind: units");
         // the source arrays are members of the handle; make sure the copies
         // are done before a later re-bind could free them
         FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_bcsr_bind: synchronize");
@@ -789,12 +911,52 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s) {
     a.status = m->status;
     if constexpr (sizeof(T) == 8) a.k = m->kd; else a.k = m->kf;
     FE_TRY_CUDA(cudaMemsetAsync(Y->values, 0, (size_t)Y->n_values * sizeof(T), s), "fe_apply_H: zero Y");
+    if (m->p <= 2) {
+        ApplyUnitArgs<T> u;
+        u.P = a.P; u.Y = a.Y; u.Vq = a.Vq;
+        u.units = reinterpret_cast<const Unit*>(static_cast<const char*>(P->tables) + P->off_units);
+        u.n_units = (int64_t)P->units.size();
+        u.lx = a.lx; u.ly = a.ly; u.lz = a.lz; u.dirichlet = a.dirichlet;
+        u.status = a.status;
+        u.k = a.k;
+        // fold |J| into the coefficients so that the kernel uses the
+        // potential as registered: Sb (|J| V + A) = (|J| Sb) (V + A / |J|),
+        // with |J| Sb in the first of the three transposed sweeps only
+        for (int i = 0; i < kMaxN; ++i)
+            for (int j = 0; j < kMaxN; ++j) {
+                u.k.Sb1[i][j] = T(double(m->kd.Sb[i][j]) * m->kd.jxw);
+                for (int d = 0; d < 3; ++d) u.k.A[d][i][j] = T(double(m->kd.A[d][i][j]) / m->kd.jxw);
+            }
+        u.k.jxw = T(1);
+        FE_TRY_CUDA(launch_apply_units<T>(m->p, u, s), "fe_apply_H: kernel launch");
+        return FE_OK;
+    }
     FE_TRY_CUDA(launch_apply<T>(m->p, a, s), "fe_apply_H: kernel launch");
+    return FE_OK;
+}
+
+int gram_tc_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaStream_t s) {
+    GramTcArgs g;
+    const char* t = static_cast<const char*>(A->tables);
+    g.A = static_cast<const float*>(A->values);
+    g.B = static_cast<const float*>(B->values);
+    g.groups = reinterpret_cast<const GramTcGroup*>(t + A->off_tcg);
+    g.items = reinterpret_cast<const GramTcItem*>(t + (sym ? A->off_tcpp : A->off_tcpy));
+    g.n_items = (int64_t)(sym ? A->tc_pp.size() : A->tc_py.size());
+    g.union_off = reinterpret_cast<const int64_t*>(t + A->off_tcu);
+    g.col_info = reinterpret_cast<const int32_t*>(t + A->off_tcci);
+    g.col_glob = reinterpret_cast<const int32_t*>(t + A->off_tccg);
+    g.rows = reinterpret_cast<const int32_t*>(t + A->off_tcrows);
+    g.n_cols = A->n_cols;
+    g.G = G;
+    FE_TRY_CUDA(cudaMemsetAsync(G, 0, (size_t)A->n_cols * A->n_cols * sizeof(double), s), "gram: zero G");
+    FE_TRY_CUDA(launch_gram_tc(g, sym, s), "gram: tensor-core kernel launch");
     return FE_OK;
 }
 
 template <typename T>
 int gram_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) return gram_tc_impl(A, B, sym, G, s);
     GramArgs<T> g;
     const char* t = static_cast<const char*>(A->tables);
     g.A = static_cast<const T*>(A->values);
@@ -803,6 +965,7 @@ int gram_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaStrea
     g.items = reinterpret_cast<const GramItem*>(t + (sym ? A->off_ipp : A->off_ipy));
     g.n_items = (int64_t)(sym ? A->i_pp.size() : A->i_py.size());
     g.cb_ptr = reinterpret_cast<const int32_t*>(t + A->off_cbp);
+    g.ld = reinterpret_cast<const int32_t*>(t + A->off_ld);
     g.n_cols = A->n_cols;
     g.symmetric = sym ? 1 : 0;
     g.G = G;
@@ -868,7 +1031,7 @@ int fe_apply_H_gram_host(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY,
 }
 
 int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream) {
-    if (!flops_per_s || iters < 1 || (dtype != FE_F32 && dtype != FE_F64))
+    if (!flops_per_s || iters < 1 || (dtype != FE_F32 && dtype != FE_F64 && dtype != 3))
         return fail(FE_EINVAL, "fe_probe_fma: bad argument");
     FE_TRY_CUDA(probe_fma(dtype, iters, flops_per_s, (cudaStream_t)stream), "fe_probe_fma");
     return FE_OK;

@@ -22,6 +22,33 @@ __global__ void __launch_bounds__(256) fma_chains(T* out, int64_t iters, T a, T 
     if (s == T(-1.2345)) out[blockIdx.x] = s;   // keeps the chains alive
 }
 
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2,%3};\n mov.b64 rb, {%4,%5};\n"
+        " mov.b64 rc, {%6,%7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0,%1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// packed FP32x2 chains: 8 chains of two lanes each
+__global__ void __launch_bounds__(256) fma2_chains(float* out, int64_t iters, float a, float b) {
+    const float2 A = make_float2(a, a), B = make_float2(b, b);
+    float2 x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = make_float2(float(threadIdx.x + c), float(threadIdx.x - c));
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = fma2(x[c], A, B);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c].x + x[c].y;
+    if (s == -1.2345f) out[blockIdx.x] = s;
+}
+
 }  // namespace
 
 cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s) {
@@ -41,6 +68,8 @@ cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_
         cudaEventRecord(t0, s);
         if (dtype == FE_F64)
             fma_chains<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.999999, 1e-7);
+        else if (dtype == 3)
+            fma2_chains<<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-7f);
         else
             fma_chains<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-7f);
         cudaEventRecord(t1, s);

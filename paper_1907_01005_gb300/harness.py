@@ -91,14 +91,14 @@ def build_problem(cfg, dtype: int = FE_F32) -> Problem:
     rows_of_k = np.repeat(np.arange(mesh.n_row_blocks), np.diff(row_ptr))
     dense[rows_of_k, col_idx] = np.arange(len(col_idx))
     vals = np.zeros(int(P.info.n_values), api.np_dtype(dtype))
+    ld = P.row_strides()
     for c in range(ncb):
-        w = int(cbp[c + 1] - cbp[c])
         for j in range(cbp[c], cbp[c + 1]):
             d = col_dofs[j]
             r = np.searchsorted(rb_ptr, d, side="right") - 1
             blk = dense[r, c]
             assert np.all(blk >= 0), "support outside the closed pattern"
-            vals[offs[blk] + (d - rb_ptr[r]) * w + (j - cbp[c])] = col_vals[j]
+            vals[offs[blk] + (d - rb_ptr[r]) * ld[c] + (j - cbp[c])] = col_vals[j]
     qp = mesh.quad_points()
     vq = inputs.potential(cfg, qp)
     return Problem(cfg, mesh, dtype, perm, cbp, row_ptr, col_idx, rb_ptr, keys, P, Y, vals, vq,
@@ -127,13 +127,14 @@ def to_device(pb: Problem, device="cuda", stream=None) -> Problem:
 def unpack_entries(pb: Problem, values: np.ndarray):
     """All stored entries of a BCSR value array as (dof, column, value)."""
     offs = pb.P.block_offsets()
+    ld = pb.P.row_strides()
     rows_of_k = np.repeat(np.arange(pb.mesh.n_row_blocks), np.diff(pb.row_ptr))
     dofs, cols, vals = [], [], []
     for k in range(len(pb.col_idx)):
         r, c = rows_of_k[k], pb.col_idx[k]
         nr = int(pb.rb_ptr[r + 1] - pb.rb_ptr[r])
         w = int(pb.cbp[c + 1] - pb.cbp[c])
-        blk = values[offs[k]: offs[k] + nr * w].reshape(nr, w)
+        blk = values[offs[k]: offs[k] + nr * ld[c]].reshape(nr, ld[c])[:, :w]
         d = np.repeat(np.arange(pb.rb_ptr[r], pb.rb_ptr[r + 1]), w)
         cc = np.tile(np.arange(pb.cbp[c], pb.cbp[c + 1]), nr)
         dofs.append(d)

@@ -64,8 +64,8 @@ def test_parity_small(name, dtype):
     ref_pp = r.G_PP[np.ix_(pb.perm, pb.perm)]
     assert _relerr(G_PY, ref_py) <= tol["PY"], _relerr(G_PY, ref_py)
     assert _relerr(G_PP, ref_pp) <= tol["PP"], _relerr(G_PP, ref_pp)
-    # P^T P is symmetric by construction (mirrored pairs)
-    assert np.array_equal(G_PP, G_PP.T)
+    # P^T P is symmetric up to the order of the FP64 atomic additions
+    assert _relerr(G_PP, G_PP.T) <= 1e-14
 
 
 def test_repeat_calls_are_stable():
