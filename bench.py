@@ -17,6 +17,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -30,13 +31,14 @@ UNIT = "DoF*columns/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="p2")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--cpu-blocks", type=int, default=8, help="column blocks in the CPU oracle sample")
     return ap.parse_args()
 
@@ -81,11 +83,11 @@ class Clocks:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="fe_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -113,6 +115,7 @@ class Clocks:
             for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
+        os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "samples": len(sm), "reasons": sorted(reasons)}
 
@@ -236,6 +239,26 @@ def time_path(pb, steps, warmup):
     return total, per
 
 
+def time_graph(pb, steps, warmup):
+    """ms per step of the CUDA graph of the whole step (one graph launch per step)."""
+    import torch
+    from paper_1907_01005_gb300 import StepGraph
+    d = pb.dev
+    s = torch.cuda.current_stream()
+    g = StepGraph(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], s)
+    for _ in range(warmup):
+        g.launch(s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        g.launch(s)
+    e1.record(s)
+    torch.cuda.synchronize()
+    del g
+    return e0.elapsed_time(e1) / steps
+
+
 def pct(v, q):
     v = sorted(v)
     return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
@@ -259,6 +282,11 @@ def main():
     hbm_peak, peak_src = load_peaks()
     fp32_peak = max(probe_alu(1), probe_alu(3))   # scalar FFMA or packed FP32x2, whichever is faster
     fp64_peak = probe_alu(2)
+    tune_ms = None
+    if not args.no_tune:
+        from paper_1907_01005_gb300 import autotune
+        tune_ms = autotune(pb.mesh, pb.P, pb.Y)
+    knobs = pb.P.get_launch()
 
     clocks = Clocks(local)
     barrier(world)
@@ -269,6 +297,7 @@ def main():
     barrier(world)
     if pb.mesh.check_device() != 0:
         raise RuntimeError("device status word set during the timed region")
+    graph_ms = time_graph(pb, args.steps, args.warmup)
     ms_step = max_over_ranks(total_ms / args.steps, world)
     value = world * N * M / (ms_step * 1e-3)
 
@@ -289,12 +318,12 @@ def main():
                   "fp32_frac": apply_flops / t_apply / fp32_peak, "bytes": apply_bytes,
                   "flops": apply_flops},
         # sliced Gram: 6 bf16 slice products for P^T Y (3 x 3 slices, s+t <= 4),
-        # 13 for P^T P (4 x 4 slices, s+t <= 6) on half the output blocks
+        # 15 for P^T P (5 x 5 slices, s+t <= 6) on half the output blocks
         "gram_py": {"ms_p50": 1e3 * t_py, "gflops": info.gram_flops / t_py / 1e9,
                     "tc_tflops": 6 * info.gram_flops / t_py / 1e12,
                     "gbs": gram_bytes / t_py / 1e9},
         "gram_pp": {"ms_p50": 1e3 * t_pp, "gflops": info.gram_flops / t_pp / 1e9,
-                    "tc_tflops": 6.5 * info.gram_flops / t_pp / 1e12},
+                    "tc_tflops": 7.5 * info.gram_flops / t_pp / 1e12},
     }
     dom = max(("apply", t_apply), ("gram_py", t_py), ("gram_pp", t_pp), key=lambda x: x[1])[0]
     if dom == "apply":
@@ -304,7 +333,7 @@ def main():
                 "alu_frac": apply_flops / t_apply / fp32_peak}
     else:
         t = t_py if dom == "gram_py" else t_pp
-        pairs = 6 if dom == "gram_py" else 6.5
+        pairs = 6 if dom == "gram_py" else 7.5
         bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
         roof = {"kernel": dom, "bound": "tensor", "achieved": pairs * info.gram_flops / t / 1e12,
@@ -320,6 +349,9 @@ def main():
                        "stored_values": int(info.stored_entries), "tiles": int(info.n_tiles),
                        "gram_accumulate": "f64", "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (P and Y %.0f MB each)" % (info.n_values * 4 / 1e6)},
+            "launch": {"persistent": knobs[0], "ctas_per_sm": knobs[1], "cells_per_round": knobs[2],
+                       "autotune_apply_ms": tune_ms},
+            "graph_ms_per_step": graph_ms,
             "p50_ms": pct(per["step"], 0.5), "p99_ms": pct(per["step"], 0.99),
             "apply_dof_cols_per_s": N * M / t_apply,
             "gram_gflops": {"PtY": info.gram_flops / t_py / 1e9, "PtP": info.gram_flops / t_pp / 1e9},

@@ -244,6 +244,51 @@ int fe_apply_H_gram_host(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_
                          double* G_PY_host, double* G_PP_host, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Launch configuration, CUDA graph of the step, autotuner.  These shape how
+ * the kernels of Alg. 6 / Alg. 8 are launched on this GPU; the paper's method
+ * is unchanged by them (results are identical up to the order of the FP
+ * additions in the scatter).
+ * ------------------------------------------------------------------------ */
+
+/* Launch knobs of fe_apply_H for source multivector P:
+ *   persistent      0: one CTA per work unit (grid launch);
+ *                   1: persistent launch of ctas_per_sm CTAs per SM that take
+ *                      units from a work counter stored in P's table buffer
+ *                      (so two fe_apply_H calls with the same P must not run
+ *                      concurrently on different streams);
+ *   ctas_per_sm     1..32 (used by the persistent launch only);
+ *   cells_per_round 0 = automatic, or 1, 2, 4, 8 = cap on the cells of the
+ *                   patch a CTA holds at once (used by the p >= 3 kernel only).
+ * Defaults: 0, 4, 0.  FE_EINVAL for values outside these ranges. */
+int fe_bcsr_set_launch(fe_bcsr* P, int32_t persistent, int32_t ctas_per_sm, int32_t cells_per_round);
+int fe_bcsr_get_launch(const fe_bcsr* P, int32_t* persistent, int32_t* ctas_per_sm,
+                       int32_t* cells_per_round);
+
+/* CUDA graph of one fe_apply_H_gram step with the given (already bound)
+ * buffers: runs the step once eagerly on `stream` (this sets kernel
+ * attributes and checks the arguments), then captures it on a private stream
+ * and instantiates it.  The graph keeps the device pointers and launch
+ * configuration of the moment of capture: re-create it after fe_bcsr_bind,
+ * fe_mesh_set_potential or fe_bcsr_set_launch.  fe_graph_launch enqueues one
+ * step on `stream`; fe_graph_destroy releases the graph (NULL is a no-op). */
+typedef struct fe_graph fe_graph;
+int fe_graph_create(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_PY_dev, double* G_PP_dev,
+                    void* stream, fe_graph** out);
+int fe_graph_launch(fe_graph* graph, void* stream);
+int fe_graph_destroy(fe_graph* graph);
+
+/* Chooses the launch knobs of fe_apply_H for P by timing each candidate (five
+ * calls after one warm-up, CUDA events on `stream`; Y is overwritten) and
+ * sets the fastest with fe_bcsr_set_launch.  With a non-empty cache_path the
+ * choice is looked up first (JSON lines, key = degree, dtype and work-list
+ * sizes; the last matching line wins) and appended after a search.
+ * *best_ms (may be NULL) receives the winner's time per call, or -1 on a
+ * cache hit.  Candidates: p <= 2 grid launch and persistent with
+ * 2..8 CTAs/SM; p >= 3 cells_per_round 8, 4, 2, 1. */
+int fe_autotune(fe_mesh* mesh, fe_bcsr* P, fe_bcsr* Y, const char* cache_path, void* stream,
+                double* best_ms);
+
+/* ------------------------------------------------------------------------
  * Measurement helper (not part of the paper's method)
  * ------------------------------------------------------------------------ */
 

@@ -5,7 +5,8 @@ ABI, include/fe_mf.h); this package is its ctypes binding.
 """
 from ._capi import (FE_EDEVICE, FE_EINVAL, FE_ENOMEM, FE_EPATTERN, FE_ESTATE, FE_ECUDA,
                     FE_EUNSUPPORTED, FE_F32, FE_F64, FE_OK, FeError, check, last_error, load)
-from .api import (BCSR, Mesh, apply_H, apply_H_gram, apply_H_gram_host, gram_PtP, gram_PtY)
+from .api import (BCSR, Mesh, StepGraph, apply_H, apply_H_gram, apply_H_gram_host, autotune, gram_PtP,
+                  gram_PtY)
 
 __all__ = ["Mesh", "BCSR", "apply_H", "gram_PtY", "gram_PtP", "apply_H_gram", "apply_H_gram_host",
-           "FeError", "FE_F32", "FE_F64", "load", "check", "last_error"]
+           "StepGraph", "autotune", "FeError", "FE_F32", "FE_F64", "load", "check", "last_error"]

@@ -84,6 +84,12 @@ SIGNATURES = {
     "fe_gram_PtP": [_P, _P, _P],
     "fe_apply_H_gram": [_P, _P, _P, _P, _P, _P],
     "fe_apply_H_gram_host": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "fe_bcsr_set_launch": [_P, _i32, _i32, _i32],
+    "fe_bcsr_get_launch": [_P, _pi32, _pi32, _pi32],
+    "fe_graph_create": [_P, _P, _P, _P, _P, _P, C.POINTER(_P)],
+    "fe_graph_launch": [_P, _P],
+    "fe_graph_destroy": [_P],
+    "fe_autotune": [_P, _P, _P, C.c_char_p, _P, _pdbl],
     "fe_probe_fma": [_i32, _i64, _pdbl, _P],
 }
 

@@ -180,6 +180,14 @@ class BCSR:
         check(capi.fe_bcsr_bind(self.h, _dptr(values), _dptr(tables), _stream(stream)))
         return self
 
+    def set_launch(self, persistent: int, ctas_per_sm: int = 4, cells_per_round: int = 0):
+        check(capi.fe_bcsr_set_launch(self.h, int(persistent), int(ctas_per_sm), int(cells_per_round)))
+
+    def get_launch(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        check(capi.fe_bcsr_get_launch(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
 
 def apply_H(mesh: Mesh, P: BCSR, Y: BCSR, stream=None):
     check(capi.fe_apply_H(mesh.h, P.h, Y.h, _stream(stream)))
@@ -202,3 +210,30 @@ def apply_H_gram_host(mesh: Mesh, P: BCSR, Y: BCSR, G_PY, G_PP, P_host, Y_host, 
     """Host-buffer variant: torch CPU tensors (pinned for full bandwidth)."""
     check(capi.fe_apply_H_gram_host(mesh.h, P.h, Y.h, _dptr(G_PY), _dptr(G_PP), _dptr(P_host),
                                     _dptr(Y_host), _dptr(G_PY_host), _dptr(G_PP_host), _stream(stream)))
+
+
+def autotune(mesh: Mesh, P: BCSR, Y: BCSR, cache_path: str | None = None, stream=None) -> float:
+    """Times the launch candidates of fe_apply_H and keeps the fastest on P;
+    returns its ms per call (-1 on a cache hit)."""
+    ms = C.c_double()
+    path = cache_path.encode() if cache_path else None
+    check(capi.fe_autotune(mesh.h, P.h, Y.h, path, _stream(stream), C.byref(ms)))
+    return ms.value
+
+
+class StepGraph:
+    """CUDA graph of one apply_H_gram step over fixed buffers (fe_graph_*)."""
+
+    def __init__(self, mesh: Mesh, P: BCSR, Y: BCSR, G_PY, G_PP, stream=None):
+        self._keep = (mesh, P, Y, G_PY, G_PP)
+        h = C.c_void_p()
+        check(capi.fe_graph_create(mesh.h, P.h, Y.h, _dptr(G_PY), _dptr(G_PP), _stream(stream), C.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        check(capi.fe_graph_launch(self.h, _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and capi._lib is not None:
+            capi.fe_graph_destroy(self.h)
+            self.h = None

@@ -16,6 +16,8 @@
 // U_b[node][ld_b]; the cells add their results into a matching tensor with
 // shared-memory atomics; the scatter adds 16-byte chunks into Y with vector
 // reductions (red.global.add.v4.f32), 4x fewer than scalar atomics.
+#include <algorithm>
+
 #include "fe_internal.h"
 
 namespace femf {
@@ -83,8 +85,16 @@ struct UnitGeo {
     static constexpr size_t bytes = (size_t)(TEN + 8 * N3) * sizeof(T);
 };
 
+// resident CTAs per SM the register budget must allow: FP32 is bounded by
+// shared memory at 5-6 CTAs of 8 warps, FP64 at 2-3 (the persistent loop
+// otherwise lets the compiler keep loop-invariant values in registers and
+// trade two resident CTAs for them)
+template <typename T>
+constexpr int kUnitMinBlocks = sizeof(T) == 4 ? 5 : 2;
+
 template <typename T, int P, int LPT_>
-__global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS) apply_unit_kernel(const ApplyUnitArgs<T> a) {
+__global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T>)
+    apply_unit_kernel(const ApplyUnitArgs<T> a) {
     using G = UnitGeo<T, P, LPT_>;
     using LN = Lanes<T, LPT_>;
     using V = typename LN::V;
@@ -104,10 +114,20 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS) apply_unit_kerne
     __shared__ int sChB[SLOTS], sChC[SLOTS], sNch, sTen;
     __shared__ int sNode[NPN];                     // (slot << 16) | row, or -1 on the boundary
 
-    const Unit& unit = a.units[blockIdx.x];
+    __shared__ int64_t sItem;
     const int tid = threadIdx.x;
-    const int px = unit.pxyz & 1023, py = (unit.pxyz >> 10) & 1023, pz = unit.pxyz >> 20;
     constexpr int kElem16 = 16 / sizeof(T);      // elements per 16-byte offset unit
+    // One unit per CTA, or (persistent launch) units pulled from a ticket
+    // counter until the list is exhausted.
+    int64_t item = blockIdx.x;
+    if (a.ticket) {
+        if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);
+        __syncthreads();
+        item = sItem;
+    }
+    while (item < a.n_units) {
+    const Unit& unit = a.units[item];
+    const int px = unit.pxyz & 1023, py = (unit.pxyz >> 10) & 1023, pz = unit.pxyz >> 20;
 
     // ---- unit tables --------------------------------------------------------
     if (tid < L) {
@@ -310,6 +330,12 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS) apply_unit_kerne
             if (nz) red_chunk(a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld + c0, v);
         }
     }
+    if (!a.ticket) break;
+    __syncthreads();                                   // shared tables are rebuilt for the next unit
+    if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);
+    __syncthreads();
+    item = sItem;
+    }
 }
 
 template <typename T, int P, int LPT>
@@ -324,7 +350,14 @@ cudaError_t launch_units_p(const ApplyUnitArgs<T>& a, cudaStream_t s) {
         attr = true;
     }
     if (a.n_units == 0) return cudaSuccess;
-    apply_unit_kernel<T, P, LPT><<<(unsigned)a.n_units, G::THREADS, G::bytes, s>>>(a);
+    unsigned grid = (unsigned)a.n_units;
+    if (a.ticket) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = (unsigned)std::min<int64_t>(a.n_units, (int64_t)sms * std::max(1, a.ctas_per_sm));
+    }
+    apply_unit_kernel<T, P, LPT><<<grid, G::THREADS, G::bytes, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -158,6 +158,8 @@ struct ApplyUnitArgs {
     const T* Vq;
     const Unit* units;
     int64_t n_units;
+    unsigned long long* ticket;   // persistent launch: work counter (zeroed before launch), else null
+    int32_t ctas_per_sm;          // persistent launch: CTAs per SM
     int32_t lx, ly, lz;
     int32_t dirichlet;
     int32_t* status;

@@ -8,12 +8,15 @@
 // and each inner sum over a window of <= 64 rows is an integer below 2^23, so
 // the bf16 x bf16 -> FP32 tensor-core accumulation is exact.  Slice pairs of
 // the same level L = s + t share a scale; levels above the cut-off LMAX are
-// dropped (weight below 2^(-8 (LMAX - 1)) of the leading level).  Levels 2
-// and 3 are moved to int32 accumulators every window (exact across the
-// group); levels >= 4 keep running FP32 sums, whose rounding is 2^-24 of a
-// level that is itself below 2^-16 of the result.  The levels are combined in
-// int64, converted to FP64 with integer operations only (the FP64 pipe of
-// this GPU runs at 1/64 of the FP32 rate) and added into the dense FP64
+// dropped.  Every level is summed on the tensor cores over a window of 64
+// rows only (each window sum is an integer below 2^23, exact whatever the
+// rounding of the tensor-core adder), then the levels are combined into one
+// int64 per output element (level L shifted by 8 (LMAX - L) bits), so the
+// sum over the group is exact.  Running FP32 sums over the whole group are
+// avoided on purpose: the tensor-core FP32 accumulation does not round to
+// nearest, and its bias over thousands of rows reaches 1e-10 of the result.
+// The int64 is converted to FP64 with integer operations only (the FP64 pipe
+// of this GPU runs at 1/64 of the FP32 rate) and added into the dense FP64
 // result with one atomic per output element and row-block group.
 //
 // Work item: (group of consecutive row blocks, 48 x 48 output tile of the
@@ -93,8 +96,6 @@ __device__ __forceinline__ void slice_store(uint32_t* base, int slice_words, int
 template <int SA, int SB, int LMAX, bool SYM>
 __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
     constexpr int NLEV = LMAX - 1;                 // levels 2..LMAX
-    constexpr int NEX = NLEV < 2 ? NLEV : 2;       // exact (int32-flushed) levels: 2 and 3
-    constexpr int NRUN = NLEV - NEX;               // running FP32 levels: 4..LMAX
     constexpr int SW = kTile * kRowWords;          // words per staged slice
     __shared__ __align__(16) uint32_t As[SA * SW];
     __shared__ __align__(16) uint32_t Bs[SB * SW];
@@ -165,20 +166,19 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
     __syncthreads();
 
     // ---- pass 2: sliced products over row chunks ----------------------------
-    float wacc[NEX][kNT][4];          // window accumulators of the exact levels
-    int iacc[NEX][kNT][4];
-    float racc[NRUN > 0 ? NRUN : 1][kNT][4];
+    float wacc[NLEV][kNT][4];         // window sums of each level (exact integers)
+    // all levels combined, exact over the group: a group has at most kMaxGroup
+    // row blocks of <= 512 rows, i.e. <= 64 windows; a level-2 window sum is
+    // <= 64 * 2^16 = 2^22 and is shifted by 8 (LMAX - 2) <= 32 bits, so
+    // |acc| < 64 * 2^55 = 2^61
+    long long acc[kNT][4];
 #pragma unroll
     for (int j = 0; j < kNT; ++j)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
+            acc[j][v] = 0;
 #pragma unroll
-            for (int l = 0; l < NEX; ++l) {
-                wacc[l][j][v] = 0.f;
-                iacc[l][j][v] = 0;
-            }
-#pragma unroll
-            for (int l = 0; l < (NRUN > 0 ? NRUN : 1); ++l) racc[l][j][v] = 0.f;
+            for (int l = 0; l < NLEV; ++l) wacc[l][j][v] = 0.f;
         }
     const int wm = (warp / kWarpsN) * 16, wn = (warp % kWarpsN) * (8 * kNT);
     const int gid = lane >> 2, tig = lane & 3;
@@ -250,8 +250,7 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
                         for (int t = 1; t <= SB; ++t) {
                             const int L = s + t;
                             if (L > LMAX) continue;
-                            if (L - 2 < NEX) mma_bf16(wacc[L - 2][j], af[s - 1], bf[t - 1][0], bf[t - 1][1]);
-                            else mma_bf16(racc[L - 2 - NEX][j], af[s - 1], bf[t - 1][0], bf[t - 1][1]);
+                            mma_bf16(wacc[L - 2][j], af[s - 1], bf[t - 1][0], bf[t - 1][1]);
                         }
                 }
             }
@@ -259,14 +258,15 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
         since_flush += kChunk;
         if (since_flush >= kFlushRows) {
 #pragma unroll
-            for (int l = 0; l < NEX; ++l)
+            for (int j = 0; j < kNT; ++j)
 #pragma unroll
-                for (int j = 0; j < kNT; ++j)
+                for (int v = 0; v < 4; ++v) {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        iacc[l][j][v] += __float2int_rn(wacc[l][j][v]);
+                    for (int l = 0; l < NLEV; ++l) {
+                        acc[j][v] += (long long)__float2int_rn(wacc[l][j][v]) << (8 * (NLEV - 1 - l));
                         wacc[l][j][v] = 0.f;
                     }
+                }
             since_flush = 0;
         }
         __syncthreads();
@@ -283,12 +283,9 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
             const int gm = sGcolA[m], gn = sGcolB[n];
             if (gm < 0 || gn < 0) continue;
             if (SYM && mi == ni && m > n) continue;      // lower half of a diagonal tile: mirrored below
-            long long t = 0;
+            long long t = acc[j][v];
 #pragma unroll
-            for (int l = 0; l < NEX; ++l)
-                t += (long long)(iacc[l][j][v] + __float2int_rn(wacc[l][j][v])) << (8 * (NLEV - 1 - l));
-#pragma unroll
-            for (int l = 0; l < NRUN; ++l) t += __float2ll_rn(racc[l][j][v]) << (8 * (NLEV - 1 - NEX - l));
+            for (int l = 0; l < NLEV; ++l) t += (long long)__float2int_rn(wacc[l][j][v]) << (8 * (NLEV - 1 - l));
             const double val = i64_scaled_to_double(t, sEa[m] + sEb[n] - 8 * LMAX);
             if (val == 0.0) continue;
             atomicAdd(&g.G[(int64_t)gm * g.n_cols + gn], val);
@@ -300,8 +297,15 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
 
 cudaError_t launch_gram_tc(const GramTcArgs& g, bool sym, cudaStream_t s) {
     if (g.n_items == 0) return cudaSuccess;
+    // The error is set by the residual after the last slice (|r| <= 2^(-8S-1)
+    // of the column bound) and by the first dropped level (<= 2^(-8 LMAX + 14)
+    // per product), so LMAX = S + 1 balances the two.  P^T Y: 3 slices, levels
+    // <= 4 (6 products, ~2^-25 of the result); P^T P: 5 slices, levels <= 6
+    // (15 products, ~2^-40: columns whose values span many binades within a
+    // group, as orbitals decaying across a p = 4 patch do, stay well inside
+    // a 1e-10 normwise bound).
     if (sym)
-        gram_tc_kernel<4, 4, 6, true><<<(unsigned)g.n_items, kThreads, 0, s>>>(g);
+        gram_tc_kernel<5, 5, 6, true><<<(unsigned)g.n_items, kThreads, 0, s>>>(g);
     else
         gram_tc_kernel<3, 3, 4, false><<<(unsigned)g.n_items, kThreads, 0, s>>>(g);
     return cudaGetLastError();

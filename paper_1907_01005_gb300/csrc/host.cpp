@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "fe_internal.h"
@@ -189,7 +190,9 @@ struct fe_bcsr {
     std::vector<int32_t> tc_cinfo, tc_cglob, tc_rows;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
     size_t off_tcg = 0, off_tcpy = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
-    size_t off_units = 0, off_ld = 0;
+    size_t off_units = 0, off_ld = 0, off_ticket = 0;
+    // launch configuration of the apply (set by fe_bcsr_set_launch / fe_autotune)
+    int32_t persistent = 0, ctas_per_sm = 4, cells_per_round = 0;
     int64_t active_cell_cols = 0;
     double gram_flops = 0.0;
     uint64_t fingerprint = 0;
@@ -779,6 +782,7 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_tccg = off;  off = align_up(off + b->tc_cglob.size() * sizeof(int32_t), 256);
         b->off_tcrows = off; off = align_up(off + b->tc_rows.size() * sizeof(int32_t), 256);
         b->off_units = off; off = align_up(off + b->units.size() * sizeof(Unit), 256);
+        b->off_ticket = off; off = align_up(off + 16, 256);   // work counter of the persistent launch
         b->table_bytes = off;
     } catch (const std::bad_alloc&) {
         delete b;
@@ -907,6 +911,7 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s) {
     int cpr = 8;
     int rc = choose_cells_per_round(m->p, P->wmax, P->dtype, cpr);
     if (rc) return rc;
+    if (P->cells_per_round > 0 && P->cells_per_round < cpr) cpr = P->cells_per_round;
     a.cells_per_round = cpr;
     a.status = m->status;
     if constexpr (sizeof(T) == 8) a.k = m->kd; else a.k = m->kf;
@@ -916,6 +921,12 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s) {
         u.P = a.P; u.Y = a.Y; u.Vq = a.Vq;
         u.units = reinterpret_cast<const Unit*>(static_cast<const char*>(P->tables) + P->off_units);
         u.n_units = (int64_t)P->units.size();
+        u.ticket = nullptr;
+        u.ctas_per_sm = P->ctas_per_sm;
+        if (P->persistent) {
+            u.ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(P->tables) + P->off_ticket);
+            FE_TRY_CUDA(cudaMemsetAsync(u.ticket, 0, sizeof(unsigned long long), s), "fe_apply_H: reset work counter");
+        }
         u.lx = a.lx; u.ly = a.ly; u.lz = a.lz; u.dirichlet = a.dirichlet;
         u.status = a.status;
         u.k = a.k;
@@ -1034,6 +1045,187 @@ int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream
     if (!flops_per_s || iters < 1 || (dtype != FE_F32 && dtype != FE_F64 && dtype != 3))
         return fail(FE_EINVAL, "fe_probe_fma: bad argument");
     FE_TRY_CUDA(probe_fma(dtype, iters, flops_per_s, (cudaStream_t)stream), "fe_probe_fma");
+    return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch configuration, CUDA graph of the step, autotuner
+// ---------------------------------------------------------------------------
+int fe_bcsr_set_launch(fe_bcsr* b, int32_t persistent, int32_t ctas_per_sm, int32_t cells_per_round) {
+    if (!b) return fail(FE_EINVAL, "fe_bcsr_set_launch: NULL multivector");
+    const bool cpr_ok = cells_per_round == 0 || cells_per_round == 1 || cells_per_round == 2 ||
+                        cells_per_round == 4 || cells_per_round == 8;
+    if ((persistent != 0 && persistent != 1) || ctas_per_sm < 1 || ctas_per_sm > 32 || !cpr_ok)
+        return fail(FE_EINVAL, "fe_bcsr_set_launch: persistent in {0,1}, ctas_per_sm in 1..32, "
+                               "cells_per_round in {0,1,2,4,8}");
+    b->persistent = persistent;
+    b->ctas_per_sm = ctas_per_sm;
+    b->cells_per_round = cells_per_round;
+    return FE_OK;
+}
+
+int fe_bcsr_get_launch(const fe_bcsr* b, int32_t* persistent, int32_t* ctas_per_sm, int32_t* cells_per_round) {
+    if (!b || !persistent || !ctas_per_sm || !cells_per_round) return fail(FE_EINVAL, "fe_bcsr_get_launch: NULL argument");
+    *persistent = b->persistent;
+    *ctas_per_sm = b->ctas_per_sm;
+    *cells_per_round = b->cells_per_round;
+    return FE_OK;
+}
+
+}  // extern "C"
+
+struct fe_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int fe_graph_create(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY, double* G_PP, void* stream,
+                    fe_graph** out) {
+    if (!out) return fail(FE_EINVAL, "fe_graph_create: out is NULL");
+    *out = nullptr;
+    int rc = check_pair("fe_graph_create", m, P, Y);
+    if (rc) return rc;
+    // one eager call first: kernel attributes are set outside the capture
+    rc = fe_apply_H_gram(m, P, Y, G_PY, G_PP, stream);
+    if (rc) return rc;
+    cudaStream_t cs = nullptr;
+    FE_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "fe_graph_create: stream");
+    cudaStream_t us = (cudaStream_t)stream;
+    cudaEvent_t ev = nullptr;
+    FE_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "fe_graph_create: event");
+    FE_TRY_CUDA(cudaEventRecord(ev, us), "fe_graph_create: event record");
+    FE_TRY_CUDA(cudaStreamWaitEvent(cs, ev, 0), "fe_graph_create: wait");
+    fe_graph* g = new (std::nothrow) fe_graph();
+    if (!g) return fail(FE_ENOMEM, "fe_graph_create: out of host memory");
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = fe_apply_H_gram(m, P, Y, G_PY, G_PP, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+        if (rc == FE_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "fe_graph_create: end capture");
+    } else {
+        rc = cuda_fail(e, "fe_graph_create: begin capture");
+    }
+    if (rc == FE_OK) {
+        e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "fe_graph_create: instantiate");
+    }
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(cs);
+    if (rc != FE_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return FE_OK;
+}
+
+int fe_graph_launch(fe_graph* g, void* stream) {
+    if (!g || !g->exec) return fail(FE_EINVAL, "fe_graph_launch: NULL graph");
+    FE_TRY_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "fe_graph_launch");
+    return FE_OK;
+}
+
+int fe_graph_destroy(fe_graph* g) {
+    if (!g) return FE_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return FE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+std::string tune_key(const fe_mesh* m, const fe_bcsr* P) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "p%d-dt%d-units%zu-tiles%zu-wmax%d", m->p, P->dtype,
+             P->units.size(), P->tiles.size(), P->wmax);
+    return buf;
+}
+
+bool cache_lookup(const char* path, const std::string& key, int& pers, int& cps, int& cpr) {
+    if (!path || !*path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    const std::string pat = "\"key\": \"" + key + "\"";
+    while (fgets(line, sizeof(line), f)) {
+        if (!strstr(line, pat.c_str())) continue;
+        int a, b, c2;
+        const char* p1 = strstr(line, "\"persistent\": ");
+        const char* p2 = strstr(line, "\"ctas_per_sm\": ");
+        const char* p3 = strstr(line, "\"cells_per_round\": ");
+        if (p1 && p2 && p3 && sscanf(p1, "\"persistent\": %d", &a) == 1 && sscanf(p2, "\"ctas_per_sm\": %d", &b) == 1 &&
+            sscanf(p3, "\"cells_per_round\": %d", &c2) == 1) {
+            pers = a; cps = b; cpr = c2; found = true;   // the last matching line wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_autotune(fe_mesh* m, fe_bcsr* P, fe_bcsr* Y, const char* cache_path, void* stream, double* best_ms) {
+    int rc = check_pair("fe_autotune", m, P, Y);
+    if (rc) return rc;
+    const std::string key = tune_key(m, P);
+    int pers = 0, cps = 4, cpr = 0;
+    if (cache_lookup(cache_path, key, pers, cps, cpr)) {
+        rc = fe_bcsr_set_launch(P, pers, cps, cpr);
+        if (best_ms) *best_ms = -1.0;
+        return rc;
+    }
+    struct Cand { int pers, cps, cpr; };
+    std::vector<Cand> cands;
+    if (m->p <= 2) {
+        cands.push_back({0, 4, 0});
+        for (int k : {2, 3, 4, 5, 6, 8}) cands.push_back({1, k, 0});
+    } else {
+        for (int k : {8, 4, 2, 1}) cands.push_back({0, 4, k});
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    FE_TRY_CUDA(cudaEventCreate(&e0), "fe_autotune: event");
+    FE_TRY_CUDA(cudaEventCreate(&e1), "fe_autotune: event");
+    float best = 1e30f;
+    Cand win = cands[0];
+    for (const Cand& cd : cands) {
+        fe_bcsr_set_launch(P, cd.pers, cd.cps, cd.cpr);
+        rc = fe_apply_H(m, P, Y, stream);             // warm-up, also validates the shape
+        if (rc) continue;
+        FE_TRY_CUDA(cudaEventRecord(e0, s), "fe_autotune: record");
+        const int reps = 5;
+        for (int i = 0; i < reps && rc == FE_OK; ++i) rc = fe_apply_H(m, P, Y, stream);
+        FE_TRY_CUDA(cudaEventRecord(e1, s), "fe_autotune: record");
+        FE_TRY_CUDA(cudaEventSynchronize(e1), "fe_autotune: sync");
+        if (rc) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best) { best = ms; win = cd; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    rc = fe_bcsr_set_launch(P, win.pers, win.cps, win.cpr);
+    if (rc) return rc;
+    if (best_ms) *best_ms = best;
+    if (cache_path && *cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "{\"key\": \"%s\", \"persistent\": %d, \"ctas_per_sm\": %d, \"cells_per_round\": %d, \"apply_ms\": %.5f}\n",
+                    key.c_str(), win.pers, win.cps, win.cpr, best);
+            fclose(f);
+        }
+    }
     return FE_OK;
 }
 

@@ -152,3 +152,17 @@ def test_pattern_rejections(lib):
     # empty pattern is valid
     e = BCSR(m, cbp, np.zeros(R + 1, np.int64), np.zeros(1, np.int32), 1)
     assert e.info.n_tiles == 0 and e.info.n_values == 0
+
+
+def test_launch_knobs_validated(lib):
+    from paper_1907_01005_gb300 import BCSR, FeError, Mesh
+    m = Mesh(4, 4, 4, 1, 1, 1, 2)
+    R = m.n_row_blocks
+    b = BCSR(m, np.array([0, 8], np.int32), np.arange(R + 1, dtype=np.int64), np.zeros(R, np.int32), 1)
+    assert b.get_launch() == (0, 4, 0)
+    b.set_launch(1, 6, 2)
+    assert b.get_launch() == (1, 6, 2)
+    for bad in [(2, 4, 0), (1, 0, 0), (1, 33, 0), (0, 4, -1), (0, 4, 3), (0, 4, 16)]:
+        with pytest.raises(FeError, match="fe_bcsr_set_launch"):
+            b.set_launch(*bad)
+    assert b.get_launch() == (1, 6, 2)
