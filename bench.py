@@ -200,6 +200,36 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def load_bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)).get("bf16_tflops", 1900.0) * 1e12
+    return 1900.0e12
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the FP32 p2 workload, with the SHA-256 of the kernel's source
+# file at capture time; reported only while that source is unchanged.
+_SHA_GRAM = "d1e4f249f7b1b6b19cc4d09a66ee7c90fc456b72e83413908df692248d80ffe0"
+_SHA_APPLY = "3dea669dfed34f2dd1b2dddceb1c6e9b72d71022fd8eed4cc85c7c638f22199d"
+NCU_TRAFFIC = {
+    "gram_py": ("gram_tc.cu", _SHA_GRAM, 507443712),
+    "gram_pp": ("gram_tc.cu", _SHA_GRAM, 256947200),
+    "apply": ("apply_unit.cu", _SHA_APPLY, 662714880),
+}
+
+
+def ncu_traffic(kernel, config_name):
+    import hashlib
+    if config_name != "p2" or kernel not in NCU_TRAFFIC:
+        return None
+    fname, sha, nbytes = NCU_TRAFFIC[kernel]
+    path = os.path.join(ROOT, "paper_1907_01005_gb300", "csrc", fname)
+    if hashlib.sha256(open(path, "rb").read()).hexdigest() != sha:
+        return None
+    return nbytes
+
+
 def probe_alu(dtype):
     import ctypes as C
     from paper_1907_01005_gb300 import _capi
@@ -301,45 +331,61 @@ def main():
     ms_step = max_over_ranks(total_ms / args.steps, world)
     value = world * N * M / (ms_step * 1e-3)
 
-    # algorithmic work per launch
+    # algorithmic work per launch (stored entries, not the 16-byte row padding):
+    # apply reads P and V_q and writes Y; P^T Y reads P and Y; P^T P reads P
     s = 4
     n_q = int(pb.mesh.info.n_q)
-    apply_bytes = 2 * info.n_values * s + n_q * s
-    gram_bytes = 2 * info.n_values * s
+    nnz = int(info.stored_entries)
+    apply_bytes = 2 * nnz * s + n_q * s
+    py_bytes = 2 * nnz * s
+    pp_bytes = nnz * s
     n = cfg.p + 1
     apply_flops = info.active_cell_cols * (18 * n ** 4 + 3 * n ** 3)
+    # sliced Gram: 6 bf16 slice products for P^T Y (3 x 3 slices, s+t <= 4),
+    # 15 for P^T P (5 x 5 slices, s+t <= 6) on half the output blocks
+    py_tc = 6 * info.gram_flops
+    pp_tc = 7.5 * info.gram_flops
+    bf16_peak = load_bf16_peak()
     t_apply = statistics.median(per["apply"]) * 1e-3
     t_py = statistics.median(per["gram_py"]) * 1e-3
     t_pp = statistics.median(per["gram_pp"]) * 1e-3
+
+    def bound(t, nbytes, work, peak, unit_name):
+        """roofline of one kernel: the resource whose ideal time is longest"""
+        t_mem = nbytes / (hbm_peak * 1e9)
+        t_cmp = work / peak
+        if t_mem >= t_cmp:
+            return {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": nbytes / t / 1e9 / hbm_peak}
+        return {"bound": unit_name, "achieved": work / t / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": work / t / peak}
+
     kernels = {
-        "apply": {"ms_p50": 1e3 * t_apply, "ms_p99": pct(per["apply"], 0.99),
-                  "gbs": apply_bytes / t_apply / 1e9, "hbm_frac": apply_bytes / t_apply / 1e9 / hbm_peak,
-                  "gflops": apply_flops / t_apply / 1e9,
-                  "fp32_frac": apply_flops / t_apply / fp32_peak, "bytes": apply_bytes,
-                  "flops": apply_flops},
-        # sliced Gram: 6 bf16 slice products for P^T Y (3 x 3 slices, s+t <= 4),
-        # 15 for P^T P (5 x 5 slices, s+t <= 6) on half the output blocks
-        "gram_py": {"ms_p50": 1e3 * t_py, "gflops": info.gram_flops / t_py / 1e9,
-                    "tc_tflops": 6 * info.gram_flops / t_py / 1e12,
-                    "gbs": gram_bytes / t_py / 1e9},
-        "gram_pp": {"ms_p50": 1e3 * t_pp, "gflops": info.gram_flops / t_pp / 1e9,
-                    "tc_tflops": 7.5 * info.gram_flops / t_pp / 1e12},
+        "apply": {"ms_p50": 1e3 * t_apply, "ms_p99": pct(per["apply"], 0.99), "bytes": apply_bytes,
+                  "flops": apply_flops, "gbs": apply_bytes / t_apply / 1e9,
+                  "hbm_frac": apply_bytes / t_apply / 1e9 / hbm_peak,
+                  "gflops": apply_flops / t_apply / 1e9, "fp32_frac": apply_flops / t_apply / fp32_peak,
+                  **{"roof_" + k: v for k, v in bound(t_apply, apply_bytes, apply_flops, fp32_peak, "alu").items()}},
+        "gram_py": {"ms_p50": 1e3 * t_py, "ms_p99": pct(per["gram_py"], 0.99), "bytes": py_bytes,
+                    "gflops": info.gram_flops / t_py / 1e9, "tc_tflops": py_tc / t_py / 1e12,
+                    "gbs": py_bytes / t_py / 1e9,
+                    **{"roof_" + k: v for k, v in bound(t_py, py_bytes, py_tc, bf16_peak, "tensor").items()}},
+        "gram_pp": {"ms_p50": 1e3 * t_pp, "ms_p99": pct(per["gram_pp"], 0.99), "bytes": pp_bytes,
+                    "gflops": info.gram_flops / t_pp / 1e9, "tc_tflops": pp_tc / t_pp / 1e12,
+                    "gbs": pp_bytes / t_pp / 1e9,
+                    **{"roof_" + k: v for k, v in bound(t_pp, pp_bytes, pp_tc, bf16_peak, "tensor").items()}},
     }
     dom = max(("apply", t_apply), ("gram_py", t_py), ("gram_pp", t_pp), key=lambda x: x[1])[0]
-    if dom == "apply":
-        roof = {"kernel": "apply", "bound": "hbm", "achieved": apply_bytes / t_apply / 1e9,
-                "peak": hbm_peak, "unit": "GB/s", "frac": apply_bytes / t_apply / 1e9 / hbm_peak,
-                "traffic": None, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                "alu_frac": apply_flops / t_apply / fp32_peak}
-    else:
-        t = t_py if dom == "gram_py" else t_pp
-        pairs = 6 if dom == "gram_py" else 7.5
-        bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0) \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
-        roof = {"kernel": dom, "bound": "tensor", "achieved": pairs * info.gram_flops / t / 1e12,
-                "peak": bf16, "unit": "TFLOP/s", "frac": pairs * info.gram_flops / t / 1e12 / bf16,
-                "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)",
-                "note": "achieved counts the bf16 slice products of the error-free split"}
+    kd = kernels[dom]
+    roof = {"kernel": dom, "bound": kd["roof_bound"], "achieved": kd["roof_achieved"], "peak": kd["roof_peak"],
+            "unit": kd["roof_unit"], "frac": kd["roof_frac"],
+            "traffic": ncu_traffic(dom, cfg.name),
+            "peak_source": (f"{peak_src} hbm_gbs" if kd["roof_bound"] == "hbm" else
+                            "measured fp32 FMA probe" if kd["roof_bound"] == "alu" else "measured bf16_tflops"),
+            "per_launch": "achieved = algorithmic bytes (stored entries x 4 B) / CUDA-event median"}
+    step_bytes = apply_bytes + py_bytes + pp_bytes
+    step_roof = {"bytes": step_bytes, "ideal_ms": step_bytes / (hbm_peak * 1e9) * 1e3,
+                 "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -355,7 +401,7 @@ def main():
             "p50_ms": pct(per["step"], 0.5), "p99_ms": pct(per["step"], 0.99),
             "apply_dof_cols_per_s": N * M / t_apply,
             "gram_gflops": {"PtY": info.gram_flops / t_py / 1e9, "PtP": info.gram_flops / t_pp / 1e9},
-            "kernels": kernels, "roofline": roof,
+            "kernels": kernels, "roofline": roof, "step_hbm_roofline": step_roof,
             "alu_peaks_tflops": {"fp32": probe_alu(1) / 1e12, "fp32x2": probe_alu(3) / 1e12,
                                  "fp64": fp64_peak / 1e12},
             "gpu_launches": 3 * args.steps, "clocks": clk}

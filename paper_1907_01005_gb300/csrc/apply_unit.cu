@@ -128,6 +128,23 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T
     while (item < a.n_units) {
     const Unit& unit = a.units[item];
     const int px = unit.pxyz & 1023, py = (unit.pxyz >> 10) & 1023, pz = unit.pxyz >> 20;
+    // Work-list check: the host packs 1..kUnitBlocks blocks with 1 <= width <= ld,
+    // ld a whole number of 16-byte chunks, at most L lanes and sum(ld) <= kUnitLdSum.
+    // A unit that breaks this would overrun shared memory: it sets the status
+    // word and is skipped (the same decision in every thread of the CTA).
+    bool unit_ok = unit.nb >= 1 && unit.nb <= kUnitBlocks;
+    if (unit_ok) {
+        int lds = 0, lanes = 0;
+        for (int q = 0; q < unit.nb; ++q) {
+            const int wq = unit.width[q], lq = unit.ld[q];
+            unit_ok = unit_ok && wq >= 1 && wq <= lq && lq % CH == 0;
+            lds += lq;
+            lanes += wq;
+        }
+        unit_ok = unit_ok && lds <= kUnitLdSum && lanes <= L;
+    }
+    if (!unit_ok && tid == 0) atomicExch(a.status, kDevBadTile);
+    if (unit_ok) {
 
     // ---- unit tables --------------------------------------------------------
     if (tid < L) {
@@ -330,6 +347,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T
             if (nz) red_chunk(a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld + c0, v);
         }
     }
+    }  // unit_ok
     if (!a.ticket) break;
     __syncthreads();                                   // shared tables are rebuilt for the next unit
     if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);

@@ -113,6 +113,7 @@ struct GramTcArgs {
     const int32_t* rows;        // rows of each row block
     int32_t n_cols;
     double* G;
+    int32_t* status;            // device status word (set on a malformed work item)
 };
 cudaError_t launch_gram_tc(const GramTcArgs& a, bool symmetric, cudaStream_t s);
 int gram_tc_tile();   // output tile edge of the tensor-core Gram

@@ -113,6 +113,14 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
     const int mi = it.tile & 0xffff, ni = it.tile >> 16;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nrb = gr.r1 - gr.r0;
+    // Work-list check: a group has 1..kMaxGroup row blocks and at most kMaxUnion
+    // union columns (the shared tables and the int64 bound depend on it); a
+    // malformed item sets the status word and leaves G untouched.
+    if (nrb < 1 || nrb > kMaxGroup || gr.n_u < 1 || gr.n_u > kMaxUnion || gr.width < 1 ||
+        gr.width > kMaxUnion * kMaxW || gr.k_rows > kMaxGroup * 512 || mi * kTile >= gr.width || ni * kTile >= gr.width) {
+        if (tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
+        return;
+    }
 
     // ---- group tables ------------------------------------------------------
     for (int e = tid; e < nrb * gr.n_u; e += kThreads) sOff[e] = g.union_off[gr.u_base + e];

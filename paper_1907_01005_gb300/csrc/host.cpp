@@ -727,7 +727,15 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                     cand.insert(cand.end(), col_idx + row_ptr[r1], col_idx + row_ptr[r1 + 1]);
                     std::sort(cand.begin(), cand.end());
                     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-                    if ((int)cand.size() > kMaxUnion && r1 > r) break;
+                    if ((int)cand.size() > kMaxUnion) {
+                        if (r1 == r) {
+                            delete b;
+                            return fail(FE_EUNSUPPORTED,
+                                        "fe_bcsr_create: row block %d holds %d column blocks; the FP32 Gram "
+                                        "supports at most %d per row block", r1, (int)cand.size(), kMaxUnion);
+                        }
+                        break;
+                    }
                     uni.swap(cand);
                     ++r1;
                 }
@@ -960,6 +968,7 @@ int gram_tc_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaSt
     g.rows = reinterpret_cast<const int32_t*>(t + A->off_tcrows);
     g.n_cols = A->n_cols;
     g.G = G;
+    g.status = A->mesh ? A->mesh->status : nullptr;
     FE_TRY_CUDA(cudaMemsetAsync(G, 0, (size_t)A->n_cols * A->n_cols * sizeof(double), s), "gram: zero G");
     FE_TRY_CUDA(launch_gram_tc(g, sym, s), "gram: tensor-core kernel launch");
     return FE_OK;

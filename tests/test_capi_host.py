@@ -166,3 +166,20 @@ def test_launch_knobs_validated(lib):
         with pytest.raises(FeError, match="fe_bcsr_set_launch"):
             b.set_launch(*bad)
     assert b.get_launch() == (1, 6, 2)
+
+
+def test_fp32_gram_union_limit(lib):
+    """The FP32 Gram packs at most 64 column blocks per row block; a wider row
+    block is refused at creation (FP64 has no such limit)."""
+    from paper_1907_01005_gb300 import BCSR, FE_EUNSUPPORTED, FeError, Mesh
+    m = Mesh(4, 4, 4, 1, 1, 1, 2)
+    R = m.n_row_blocks
+    ncb = 65
+    cbp = np.arange(ncb + 1, dtype=np.int32)
+    row_ptr = np.zeros(R + 1, np.int64)
+    row_ptr[1:] = ncb
+    col_idx = np.arange(ncb, dtype=np.int32)
+    with pytest.raises(FeError, match="at most 64") as e:
+        BCSR(m, cbp, row_ptr, col_idx, 1)
+    assert e.value.code == FE_EUNSUPPORTED
+    assert BCSR(m, cbp, row_ptr, col_idx, 2).info.nnz_blocks == ncb
