@@ -35,7 +35,8 @@ constexpr int kThreads = 32 * kWarpsM * kWarpsN;
 constexpr int kNT = 3;           // n8 tiles per warp (16 x 24 sub-tile)
 constexpr int kChunk = 32;       // rows staged per iteration
 constexpr int kRowWords = 20;    // 32-bit words per staged column (16 used: 32 rows of bf16)
-constexpr int kFlushRows = 64;   // rows between FP32 -> int32 flushes (window sums < 2^23)
+constexpr int kFlushRows = 64;   // rows per exact window (window sums < 2^23)
+constexpr int kMaxRows = (2 * kMaxP + 1) * (2 * kMaxP + 1) * (2 * kMaxP + 1);   // rows of a row block
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
     // union columns (the shared tables and the int64 bound depend on it); a
     // malformed item sets the status word and leaves G untouched.
     if (nrb < 1 || nrb > kMaxGroup || gr.n_u < 1 || gr.n_u > kMaxUnion || gr.width < 1 ||
-        gr.width > kMaxUnion * kMaxW || gr.k_rows > kMaxGroup * 512 || mi * kTile >= gr.width || ni * kTile >= gr.width) {
+        gr.width > kMaxUnion * kMaxW || gr.k_rows > kMaxGroup * kMaxRows || mi * kTile >= gr.width || ni * kTile >= gr.width) {
         if (tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
         return;
     }
@@ -176,9 +177,9 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
     // ---- pass 2: sliced products over row chunks ----------------------------
     float wacc[NLEV][kNT][4];         // window sums of each level (exact integers)
     // all levels combined, exact over the group: a group has at most kMaxGroup
-    // row blocks of <= 512 rows, i.e. <= 64 windows; a level-2 window sum is
-    // <= 64 * 2^16 = 2^22 and is shifted by 8 (LMAX - 2) <= 32 bits, so
-    // |acc| < 64 * 2^55 = 2^61
+    // row blocks of <= kMaxRows = 729 rows, i.e. <= 92 windows; a level-2
+    // window sum is <= 64 * 2^16 = 2^22 and is shifted by 8 (LMAX - 2) <= 32
+    // bits (the other levels add less than 2^-7 of that), so |acc| < 2^61
     long long acc[kNT][4];
 #pragma unroll
     for (int j = 0; j < kNT; ++j)
