@@ -300,6 +300,22 @@ int fe_autotune(fe_mesh* mesh, fe_bcsr* P, fe_bcsr* Y, const char* cache_path, v
  * `stream`; uses a small stream-ordered allocation. */
 int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream);
 
+/* Allocation-free variant of fe_probe_fma (the paper has no counterpart: it
+ * is a measurement helper).  Same arguments, kernels and result; the per-CTA
+ * sink of the chains lives in a static device array of 4096 doubles (32 KB)
+ * instead of a stream-ordered allocation, so the call allocates no device
+ * memory at all.  For callers that may not allocate, such as a server that
+ * has admitted work up to its device-memory budget.
+ *   - The first call on each device does a one-time set-up (it resolves the
+ *     array's device address with that device current); make that first call
+ *     before any stream capture.
+ *   - FE_EINVAL with a message when the device needs more than 4096 slots
+ *     (8 per SM, i.e. more than 512 SMs) or its ordinal is 64 or more.
+ *   - All calls share the array, which keeps the last contents; nothing in
+ *     it needs to start at zero.  Overlapping calls (other streams or host
+ *     threads) race on its contents. */
+int fe_probe_fma_static(int32_t dtype, int64_t iters, double* flops_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,7 @@ SIGNATURES = {
     "fe_graph_destroy": [_P],
     "fe_autotune": [_P, _P, _P, C.c_char_p, _P, _pdbl],
     "fe_probe_fma": [_i32, _i64, _pdbl, _P],
+    "fe_probe_fma_static": [_i32, _i64, _pdbl, _P],
 }
 
 _lib = None

@@ -177,6 +177,10 @@ template <typename T>
 cudaError_t launch_gram(const GramArgs<T>& a, cudaStream_t s);
 
 cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s);
+constexpr int kProbeSinkSlots = 4096;   // per-CTA slots of the allocation-free probe (512 SMs x 8)
+// *too_many: 0 = ran; > 0 = the device needs that many slots (> kProbeSinkSlots);
+// -1 = device ordinal beyond the per-device table
+cudaError_t probe_fma_static(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s, int* too_many);
 
 // Device status codes written by kernels.
 enum DeviceStatus : int32_t {

@@ -1057,6 +1057,21 @@ int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream
     return FE_OK;
 }
 
+int fe_probe_fma_static(int32_t dtype, int64_t iters, double* flops_per_s, void* stream) {
+    if (!flops_per_s || iters < 1 || (dtype != FE_F32 && dtype != FE_F64 && dtype != 3))
+        return fail(FE_EINVAL, "fe_probe_fma_static: bad argument");
+    int too_many = 0;
+    FE_TRY_CUDA(probe_fma_static(dtype, iters, flops_per_s, (cudaStream_t)stream, &too_many),
+                "fe_probe_fma_static");
+    if (too_many > 0)
+        return fail(FE_EINVAL,
+                    "fe_probe_fma_static: this device needs %d per-CTA sink slots (8 per SM); the static "
+                    "sink holds %d (devices of up to %d SMs)", too_many, kProbeSinkSlots, kProbeSinkSlots / 8);
+    if (too_many < 0)
+        return fail(FE_EINVAL, "fe_probe_fma_static: device ordinal beyond the 64 devices the set-up table holds");
+    return FE_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Launch configuration, CUDA graph of the step, autotuner
 // ---------------------------------------------------------------------------

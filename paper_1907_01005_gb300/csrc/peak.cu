@@ -2,6 +2,8 @@
 // cell kernels and of the FP64 Gram is reported against.  Each thread runs
 // eight independent FMA chains so that latency is hidden; the grid covers
 // every SM several times.
+#include <mutex>
+
 #include "fe_internal.h"
 
 namespace femf {
@@ -51,16 +53,11 @@ __global__ void __launch_bounds__(256) fma2_chains(float* out, int64_t iters, fl
 
 }  // namespace
 
-cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s) {
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const int blocks = sms * 8, threads = 256;
-    void* out = nullptr;
-    e = cudaMallocAsync(&out, sizeof(double) * blocks, s);
-    if (e != cudaSuccess) return e;
+// Timed launches of the chains into the per-CTA sink `out` (blocks slots).
+static cudaError_t run_probe(int dtype, int64_t iters, int blocks, void* out, double* flops_per_s,
+                             cudaStream_t s) {
+    const int threads = 256;
+    cudaError_t e = cudaSuccess;
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
@@ -79,11 +76,85 @@ cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_
     cudaEventElapsedTime(&ms, t0, t1);
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    cudaFreeAsync(out, s);
     if (e != cudaSuccess) return e;
     const double flops = 2.0 * 8 * 16 * (double)iters * blocks * threads;
     *flops_per_s = flops / (ms * 1e-3);
     return cudaGetLastError();
+}
+
+static cudaError_t probe_blocks(int& blocks) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    blocks = sms * 8;
+    return cudaSuccess;
+}
+
+cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s) {
+    int blocks = 0;
+    cudaError_t e = probe_blocks(blocks);
+    if (e != cudaSuccess) return e;
+    void* out = nullptr;
+    e = cudaMallocAsync(&out, sizeof(double) * blocks, s);
+    if (e != cudaSuccess) return e;
+    e = run_probe(dtype, iters, blocks, out, flops_per_s, s);
+    const cudaError_t ef = cudaFreeAsync(out, s);
+    return e != cudaSuccess ? e : ef;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant: the per-CTA sink lives in a file-scope device
+// array instead of a stream-ordered allocation.  It serves callers that must
+// not allocate device memory at all, e.g. a serving process that has already
+// admitted work up to its HBM budget: an allocation there can fail or take
+// memory the admitted requests were promised, and a peak measurement must not
+// disturb them.  The sink holds one slot per CTA (8 CTAs per SM); nothing in
+// it has to start at zero, because a CTA only ever writes its own slot.  All
+// calls share the array and it keeps the last contents; calls that overlap
+// in time (other streams, other host threads) write the same slots, which is
+// harmless for the probe's result but is a race on the array's contents.
+// ---------------------------------------------------------------------------
+__device__ __align__(256) double g_probe_sink[kProbeSinkSlots];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_sink_mu;
+void* g_sink_ptr[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t probe_fma_static(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s, int* too_many) {
+    *too_many = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) {
+        *too_many = -1;
+        return cudaSuccess;
+    }
+    int blocks = 0;
+    e = probe_blocks(blocks);
+    if (e != cudaSuccess) return e;
+    if (blocks > kProbeSinkSlots) {
+        *too_many = blocks;
+        return cudaSuccess;
+    }
+    void* out = nullptr;
+    {
+        // set-up once per device, with that device current: resolve the
+        // device address of the array (this is the call to make before any
+        // stream capture)
+        std::lock_guard<std::mutex> lock(g_sink_mu);
+        if (!g_sink_ptr[dev]) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_probe_sink);
+            if (e != cudaSuccess) return e;
+            g_sink_ptr[dev] = ptr;
+        }
+        out = g_sink_ptr[dev];
+    }
+    return run_probe(dtype, iters, blocks, out, flops_per_s, s);
 }
 
 }  // namespace femf
