@@ -100,6 +100,7 @@ struct GramTcGroup {
 struct GramTcItem {
     int32_t group;
     int32_t tile;       // mi | ni << 16 (square tiles of gram_tc_tile() union columns)
+    int32_t k0, k1;     // rows [k0, k1) of the group (split at gram_tc_split_rows())
 };
 struct GramTcArgs {
     const float* A;
@@ -116,7 +117,8 @@ struct GramTcArgs {
     int32_t* status;            // device status word (set on a malformed work item)
 };
 cudaError_t launch_gram_tc(const GramTcArgs& a, bool symmetric, cudaStream_t s);
-int gram_tc_tile();   // output tile edge of the tensor-core Gram
+int gram_tc_tile();         // output super-tile edge of the tensor-core Gram
+int gram_tc_split_rows();   // rows per work item (multiple of every window height)
 
 template <typename T>
 struct ApplyArgs {

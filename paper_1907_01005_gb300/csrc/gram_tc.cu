@@ -1,27 +1,38 @@
 // Gram products of FP32 multivectors on the tensor cores with an error-free
 // split (C = A^T B over stored blocks, Alg. 8; FP64-accurate accumulation).
 //
-// Every FP32 value of a column m of the group slab is written as a sum of S
-// slices q_s 2^(E_m - 8 s) with integers |q_s| <= 256 (exact in bf16), E_m a
-// power-of-two bound of the column's magnitude over the group's rows.  Then
-//   sum_k a_km b_kn = sum_{s,t} 2^(E_m + F_n - 8(s+t)) sum_k q_s,km r_t,kn ,
-// and each inner sum over a window of <= 64 rows is an integer below 2^23, so
-// the bf16 x bf16 -> FP32 tensor-core accumulation is exact.  Slice pairs of
-// the same level L = s + t share a scale; levels above the cut-off LMAX are
-// dropped.  Every level is summed on the tensor cores over a window of 64
-// rows only (each window sum is an integer below 2^23, exact whatever the
-// rounding of the tensor-core adder), then the levels are combined into one
-// int64 per output element (level L shifted by 8 (LMAX - L) bits), so the
-// sum over the group is exact.  Running FP32 sums over the whole group are
-// avoided on purpose: the tensor-core FP32 accumulation does not round to
-// nearest, and its bias over thousands of rows reaches 1e-10 of the result.
-// The int64 is converted to FP64 with integer operations only (the FP64 pipe
-// of this GPU runs at 1/64 of the FP32 rate) and added into the dense FP64
-// result with one atomic per output element and row-block group.
+// Rows are processed in windows of KW rows.  In a window every FP32 value x
+// of union column m is normalised by the window's own power-of-two bound
+// 2^E (|x| < 2^E, E per column and window) and written as a sum of slices
+//   x 2^-E = sum_s y_s ,  y_s = q_s 2^(-8 s),  q_s integer, |q_s| <= 256,
+// so every y_s is exact in bf16 and every slice product is exact in FP32.
+// The product of slices s and t belongs to level L = s + t (weight
+// 2^(-8 L)); levels above LMAX are dropped.  Per window the tensor cores
+// (mma.sync m16n8k16, bf16 -> FP32) sum
+//   level 2 and level 3 in accumulators of their own: their window sums are
+//     integers (in units of 2^-16, 2^-24) below 2^23, hence exact whatever
+//     the rounding of the tensor-core adder;
+//   levels 4..LMAX together in a third accumulator: their weight is below
+//     2^-32 of the result, so the FP32 rounding there is immaterial.
+// After each window the three sums are converted to integers in units of
+// 2^-(8 LMAX) and combined into an int64 per output element, scaled by
+// 2^(E_m(w) + E_n(w)) relative to a running per-column reference exponent
+// R (the largest window exponent seen so far): the accumulator is shifted
+// right when R grows and the window value when it is below R.  The dropped
+// bits are below 2^-(8 LMAX) of the reference scale per window.
 //
-// Work item: (group of consecutive row blocks, 48 x 48 output tile of the
-// group's union columns); 6 warps in a 3 x 2 layout, each owning a 16 x 24
-// sub-tile (three m16n8k16 tiles).
+// The error is set by the residual after the last slice (2^(-8S-1) of the
+// column bound) and by the first dropped level: P^T Y uses 3 slices and
+// levels <= 4 (6 products, ~2^-25), P^T P 5 slices and levels <= 6
+// (15 products, ~2^-40).  The int64 is converted to FP64 with integer
+// operations only (the FP64 pipe of this GPU runs at 1/64 of the FP32
+// rate) and added into the dense FP64 result with one atomic per element.
+//
+// Work item: (group of consecutive row blocks, 64 x 64 super-tile of the
+// group's union columns, range of the group's rows).  8 warps, each owning
+// a 16 x 32 sub-tile (four m16n8k16 tiles); slices are staged in shared
+// memory as [column][row] bf16 rows with XOR-swizzled 16-byte chunks and
+// read with ldmatrix.
 #include <cuda_bf16.h>
 
 #include "fe_internal.h"
@@ -29,13 +40,9 @@
 namespace femf {
 namespace {
 
-constexpr int kTile = 48;        // output tile edge (union columns)
-constexpr int kWarpsM = 3, kWarpsN = 2;
-constexpr int kThreads = 32 * kWarpsM * kWarpsN;
-constexpr int kNT = 3;           // n8 tiles per warp (16 x 24 sub-tile)
-constexpr int kChunk = 32;       // rows staged per iteration
-constexpr int kRowWords = 20;    // 32-bit words per staged column (16 used: 32 rows of bf16)
-constexpr int kFlushRows = 64;   // rows per exact window (window sums < 2^23)
+constexpr int kST = 64;          // super-tile edge (union columns)
+constexpr int kThreads = 256;    // 8 warps: 4 (m16) x 2 (n32)
+constexpr int kNone = -30000;    // exponent of an all-zero column
 constexpr int kMaxRows = (2 * kMaxP + 1) * (2 * kMaxP + 1) * (2 * kMaxP + 1);   // rows of a row block
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -46,10 +53,11 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// word index of (column row, word kw = k/2) in a staged slice, XOR-swizzled
-// so that 32 consecutive columns with the same kw hit 32 different banks and
-// the fragment loads (8 columns x 4 words) stay conflict-free
-__device__ __forceinline__ int swz(int col, int kw) { return col * kRowWords + (kw ^ ((col >> 3) & 3)); }
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], unsigned addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
 
 // t * 2^e2 as a double, from integer operations only (round to nearest even)
 __device__ __forceinline__ double i64_scaled_to_double(long long t, int e2) {
@@ -78,248 +86,289 @@ __device__ __forceinline__ double i64_scaled_to_double(long long t, int e2) {
     return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
 }
 
-// slices of two rows (x0, x1) of one column, already normalised to |x| < 1:
-// q_s = rint(r 2^(8s)), r -= q_s 2^(-8s); stored as packed bf16 pairs
-template <int S>
-__device__ __forceinline__ void slice_store(uint32_t* base, int slice_words, int word, float x0, float x1) {
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }   // |e| <= 126
+
+// Shared-memory byte offset of (column c, 16-byte chunk kc) in a slice of
+// kST columns x KW rows: chunks are XOR-swizzled by the column's low 3 bits
+// so that ldmatrix (8 columns, same chunk) and the staging stores hit 8
+// different bank groups.
+template <int KW>
+__device__ __forceinline__ unsigned chunk_off(int c, int kc) {
+    return (unsigned)(c * (KW * 2) + ((kc ^ (c & 7)) << 4));
+}
+
+// Per-window state of one operand's 64 columns.
+struct ColState {
+    int* R;        // running reference exponent
+    int* dR;       // growth of R in this window (accumulator right shift)
+    int* dW;       // R - E(w) (window value right shift), 63 for an empty column
+    float* f1;     // 2^-(E>>1)   } x 2^-E = (x * f1) * f2 without underflow
+    float* f2;     // 2^-(E-(E>>1))
+};
+
+// Loads a window of one operand into registers: thread (column c, segment
+// seg) holds rows row0 .. row0+SEG-1 of column c; returns max |x|.
+template <int SEG>
+__device__ __forceinline__ float load_window(const float* __restrict__ X, int ci, const int64_t* sOff, int n_u,
+                                             const int* sRowRb, const int* sRowLoc, int row0, float (&v)[SEG]) {
+    float mx = 0.f;
+    const int slot = ci >> 16, a = (ci >> 8) & 0xff, ld = ci & 0xff;
 #pragma unroll
-    for (int s = 1; s <= S; ++s) {
-        const float up = __int_as_float((127 + 8 * s) << 23);   // 2^(8s)
-        const float dn = __int_as_float((127 - 8 * s) << 23);   // 2^(-8s)
-        const float q0 = rintf(x0 * up), q1 = rintf(x1 * up);
-        x0 = fmaf(-q0, dn, x0);
-        x1 = fmaf(-q1, dn, x1);
-        const __nv_bfloat162 v = __floats2bfloat162_rn(q0, q1);
-        base[(s - 1) * slice_words + word] = *reinterpret_cast<const uint32_t*>(&v);
+    for (int i = 0; i < SEG; ++i) {
+        v[i] = 0.f;
+        const int r = sRowRb[row0 + i];
+        if (ci >= 0 && r >= 0) {
+            const int64_t o = sOff[r * n_u + slot];
+            if (o >= 0) v[i] = __ldg(X + o + (int64_t)sRowLoc[row0 + i] * ld + a);
+        }
+        mx = fmaxf(mx, fabsf(v[i]));
+    }
+    return mx;
+}
+
+// Column exponent of this window and the reference update.
+__device__ __forceinline__ void window_exponent(float mx, int c, const ColState& st) {
+    const int E = mx > 0.f ? ilogbf(mx) + 1 : kNone;
+    const int R = st.R[c];
+    const int newR = E > R ? E : R;
+    st.dR[c] = (R == kNone) ? 0 : min(newR - R, 63);
+    st.dW[c] = (E == kNone) ? 63 : min(newR - E, 63);
+    st.R[c] = newR;
+    const int e = (E == kNone) ? 0 : E;
+    st.f1[c] = pow2f(-(e >> 1));
+    st.f2[c] = pow2f(-(e - (e >> 1)));
+}
+
+// Slices a thread's SEG values (column c, rows seg*SEG ..) into S bf16
+// slices y_s = q_s 2^(-8 s) and stores them as SEG/8 16-byte chunks each.
+template <int S, int SEG, int KW>
+__device__ __forceinline__ void slice_store(unsigned char* base, int c, int seg, float f1, float f2,
+                                            const float (&v)[SEG]) {
+    constexpr int SLICE = kST * KW * 2;
+#pragma unroll
+    for (int ch = 0; ch < SEG / 8; ++ch) {
+        float r[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r[i] = (v[ch * 8 + i] * f1) * f2;
+        const unsigned off = chunk_off<KW>(c, seg * (SEG / 8) + ch);
+#pragma unroll
+        for (int s = 1; s <= S; ++s) {
+            const float up = pow2f(8 * s), dn = pow2f(-8 * s);
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float q0 = rintf(r[2 * i] * up), q1 = rintf(r[2 * i + 1] * up);
+                r[2 * i] = fmaf(-q0, dn, r[2 * i]);
+                r[2 * i + 1] = fmaf(-q1, dn, r[2 * i + 1]);
+                const __nv_bfloat162 b = __floats2bfloat162_rn(q0 * dn, q1 * dn);   // exact
+                w[i] = *reinterpret_cast<const uint32_t*>(&b);
+            }
+            *reinterpret_cast<uint4*>(base + (s - 1) * SLICE + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
     }
 }
 
-template <int SA, int SB, int LMAX, bool SYM>
-__global__ void __launch_bounds__(kThreads) gram_tc_kernel(const GramTcArgs g) {
-    constexpr int NLEV = LMAX - 1;                 // levels 2..LMAX
-    constexpr int SW = kTile * kRowWords;          // words per staged slice
-    __shared__ __align__(16) uint32_t As[SA * SW];
-    __shared__ __align__(16) uint32_t Bs[SB * SW];
-    __shared__ int sEa[kTile], sEb[kTile];
-    __shared__ float sNa[kTile], sNb[kTile];
-    __shared__ unsigned sMaxA[kTile], sMaxB[kTile];
+template <int SA, int SB, int LMAX, bool SYM, int KW>
+__global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g) {
+    static_assert(KW % 32 == 0 && KW <= 128, "window rows");
+    constexpr int SEG = KW / 4;                   // rows per staging thread
+    constexpr int SLICE = kST * KW * 2;           // bytes per staged slice
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* As = smem;
+    unsigned char* Bs = smem + SA * SLICE;
     __shared__ int64_t sOff[kMaxGroup * kMaxUnion];
-    __shared__ int sColA[kTile], sColB[kTile];     // (u << 16) | (a << 8) | w, or -1
-    __shared__ int sGcolA[kTile], sGcolB[kTile];
-    __shared__ int sRowRb[kChunk], sRowLoc[kChunk];
+    __shared__ int sColA[kST], sColB[kST], sGcolA[kST], sGcolB[kST];
+    __shared__ int sRowRb[KW], sRowLoc[KW];
     __shared__ int sPref[kMaxGroup + 1];
+    __shared__ float sMax[2][4][kST];
+    __shared__ int sR[2][kST], sDR[2][kST], sDW[2][kST];
+    __shared__ float sF1[2][kST], sF2[2][kST];
 
     const GramTcItem it = g.items[blockIdx.x];
     const GramTcGroup gr = g.groups[it.group];
     const int mi = it.tile & 0xffff, ni = it.tile >> 16;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nrb = gr.r1 - gr.r0;
-    // Work-list check: a group has 1..kMaxGroup row blocks and at most kMaxUnion
-    // union columns (the shared tables and the int64 bound depend on it); a
-    // malformed item sets the status word and leaves G untouched.
+    // Work-list check: a group has 1..kMaxGroup row blocks of at most kMaxRows
+    // rows and at most kMaxUnion union column blocks (the shared tables and
+    // the int64 bound depend on it); a malformed item sets the status word
+    // and leaves G untouched.
     if (nrb < 1 || nrb > kMaxGroup || gr.n_u < 1 || gr.n_u > kMaxUnion || gr.width < 1 ||
-        gr.width > kMaxUnion * kMaxW || gr.k_rows > kMaxGroup * kMaxRows || mi * kTile >= gr.width || ni * kTile >= gr.width) {
+        gr.width > kMaxUnion * kMaxW || gr.k_rows > kMaxGroup * kMaxRows || mi * kST >= gr.width ||
+        ni * kST >= gr.width || it.k0 < 0 || it.k1 > gr.k_rows || it.k0 >= it.k1) {
         if (tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
         return;
     }
+    const bool diag = SYM && mi == ni;            // B's columns are A's columns
 
     // ---- group tables ------------------------------------------------------
     for (int e = tid; e < nrb * gr.n_u; e += kThreads) sOff[e] = g.union_off[gr.u_base + e];
-    if (tid < kTile) {
-        const int ma = mi * kTile + tid, nb = ni * kTile + tid;
+    if (tid < kST) {
+        const int ma = mi * kST + tid, nb = ni * kST + tid;
         sColA[tid] = ma < gr.width ? g.col_info[gr.c_base + ma] : -1;
         sGcolA[tid] = ma < gr.width ? g.col_glob[gr.c_base + ma] : -1;
         sColB[tid] = nb < gr.width ? g.col_info[gr.c_base + nb] : -1;
         sGcolB[tid] = nb < gr.width ? g.col_glob[gr.c_base + nb] : -1;
-        sMaxA[tid] = 0u;
-        sMaxB[tid] = 0u;
+        sR[0][tid] = kNone;
+        sR[1][tid] = kNone;
     }
     if (tid == 0) {
         sPref[0] = 0;
         for (int r = 0; r < nrb; ++r) sPref[r + 1] = sPref[r] + g.rows[gr.r0 + r];
     }
-    __syncthreads();
 
-    // ---- pass 1: column magnitude bounds (|x| < 2^E) over the group --------
-    {
-        const int col = tid % kTile, ph = tid / kTile, nph = kThreads / kTile;
-        const int ca = sColA[col], cb = sColB[col];
-        float ma = 0.f, mb = 0.f;
-        for (int r = 0; r < nrb; ++r) {
-            const int rows = sPref[r + 1] - sPref[r];
-            if (ca >= 0) {
-                const int64_t o = sOff[r * gr.n_u + (ca >> 16)];
-                const int a = (ca >> 8) & 0xff, w = ca & 0xff;
-                if (o >= 0)
-                    for (int k = ph; k < rows; k += nph) ma = fmaxf(ma, fabsf(g.A[o + (int64_t)k * w + a]));
-            }
-            if (cb >= 0) {
-                const int64_t o = sOff[r * gr.n_u + (cb >> 16)];
-                const int a = (cb >> 8) & 0xff, w = cb & 0xff;
-                if (o >= 0)
-                    for (int k = ph; k < rows; k += nph) mb = fmaxf(mb, fabsf(g.B[o + (int64_t)k * w + a]));
-            }
-        }
-        atomicMax(&sMaxA[col], __float_as_uint(ma));   // non-negative floats order as unsigned
-        atomicMax(&sMaxB[col], __float_as_uint(mb));
-    }
-    __syncthreads();
-    if (tid < kTile) {
-        const float ma = __uint_as_float(sMaxA[tid]), mb = __uint_as_float(sMaxB[tid]);
-        const int ea = ma > 0.f ? ilogbf(ma) + 1 : 0, eb = mb > 0.f ? ilogbf(mb) + 1 : 0;
-        sEa[tid] = ea;
-        sEb[tid] = eb;
-        sNa[tid] = ma > 0.f ? scalbnf(1.0f, -ea) : 0.f;
-        sNb[tid] = mb > 0.f ? scalbnf(1.0f, -eb) : 0.f;
-    }
-    __syncthreads();
-
-    // ---- pass 2: sliced products over row chunks ----------------------------
-    float wacc[NLEV][kNT][4];         // window sums of each level (exact integers)
-    // all levels combined, exact over the group: a group has at most kMaxGroup
-    // row blocks of <= kMaxRows = 729 rows, i.e. <= 92 windows; a level-2
-    // window sum is <= 64 * 2^16 = 2^22 and is shifted by 8 (LMAX - 2) <= 32
-    // bits (the other levels add less than 2^-7 of that), so |acc| < 2^61
-    long long acc[kNT][4];
-#pragma unroll
-    for (int j = 0; j < kNT; ++j)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            acc[j][v] = 0;
-#pragma unroll
-            for (int l = 0; l < NLEV; ++l) wacc[l][j][v] = 0.f;
-        }
-    const int wm = (warp / kWarpsN) * 16, wn = (warp % kWarpsN) * (8 * kNT);
+    const ColState stA{sR[0], sDR[0], sDW[0], sF1[0], sF2[0]};
+    const ColState stB{sR[1], sDR[1], sDW[1], sF1[1], sF2[1]};
+    const int bo = diag ? 0 : 1;                  // operand index of B's column state
+    const int wm = (warp >> 1) * 16, wn = (warp & 1) * 32;
     const int gid = lane >> 2, tig = lane & 3;
-    const bool wact = (mi * kTile + wm < gr.width) && (ni * kTile + wn < gr.width) &&
-                      (!SYM || mi < ni || wm < wn + 8 * kNT);   // skip sub-tiles beyond the union
+    const bool wact = (mi * kST + wm < gr.width) && (ni * kST + wn < gr.width) && (!diag || wm < wn + 32);
+    const int c = tid & (kST - 1), seg = tid >> 6;
 
-    int since_flush = 0;
-    for (int k0 = 0; k0 < gr.k_rows; k0 += kChunk) {
-        if (tid < kChunk) {
+    long long acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[j][v] = 0;
+
+    const unsigned As_s = (unsigned)__cvta_generic_to_shared(As);
+    const unsigned Bs_s = (unsigned)__cvta_generic_to_shared(diag ? As : Bs);
+
+    for (int k0 = it.k0; k0 < it.k1; k0 += KW) {
+        __syncthreads();                           // tables ready; previous window's MMAs and flush done
+        if (tid < KW) {
             const int k = k0 + tid;
             int r = -1, loc = 0;
-            if (k < gr.k_rows) {
+            if (k < it.k1 && k < sPref[nrb]) {
                 r = 0;
-                while (k >= sPref[r + 1]) ++r;
+                while (r < nrb - 1 && k >= sPref[r + 1]) ++r;
                 loc = k - sPref[r];
             }
             sRowRb[tid] = r;
             sRowLoc[tid] = loc;
         }
         __syncthreads();
-        // stage: each thread takes (column, pair of rows)
-        for (int e = tid; e < kTile * (kChunk / 2); e += kThreads) {
-            const int col = e % kTile, kw = e / kTile;
-            float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-            const int ca = sColA[col], cb = sColB[col];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = sRowRb[2 * kw + h];
-                if (r < 0) continue;
-                const int loc = sRowLoc[2 * kw + h];
-                if (ca >= 0) {
-                    const int64_t o = sOff[r * gr.n_u + (ca >> 16)];
-                    if (o >= 0) (h ? a1 : a0) = g.A[o + (int64_t)loc * (ca & 0xff) + ((ca >> 8) & 0xff)];
-                }
-                if (cb >= 0) {
-                    const int64_t o = sOff[r * gr.n_u + (cb >> 16)];
-                    if (o >= 0) (h ? b1 : b0) = g.B[o + (int64_t)loc * (cb & 0xff) + ((cb >> 8) & 0xff)];
-                }
-            }
-            const int wd = swz(col, kw);
-            slice_store<SA>(As, SW, wd, a0 * sNa[col], a1 * sNa[col]);
-            slice_store<SB>(Bs, SW, wd, b0 * sNb[col], b1 * sNb[col]);
+        // ---- load the window, column bounds, exponents ----------------------
+        float va[SEG], vb[SEG];
+        sMax[0][seg][c] = load_window<SEG>(g.A, sColA[c], sOff, gr.n_u, sRowRb, sRowLoc, seg * SEG, va);
+        if (!diag) sMax[1][seg][c] = load_window<SEG>(g.B, sColB[c], sOff, gr.n_u, sRowRb, sRowLoc, seg * SEG, vb);
+        __syncthreads();
+        if (tid < kST) {
+            window_exponent(fmaxf(fmaxf(sMax[0][0][tid], sMax[0][1][tid]), fmaxf(sMax[0][2][tid], sMax[0][3][tid])),
+                            tid, stA);
+        } else if (tid < 2 * kST && !diag) {
+            const int cb = tid - kST;
+            window_exponent(fmaxf(fmaxf(sMax[1][0][cb], sMax[1][1][cb]), fmaxf(sMax[1][2][cb], sMax[1][3][cb])),
+                            cb, stB);
         }
         __syncthreads();
-        if (wact) {
+        // ---- slices -----------------------------------------------------------
+        slice_store<SA, SEG, KW>(As, c, seg, sF1[0][c], sF2[0][c], va);
+        if (!diag) slice_store<SB, SEG, KW>(Bs, c, seg, sF1[1][c], sF2[1][c], vb);
+        __syncthreads();
+        if (!wact) continue;
+
+        // ---- tensor-core products of the window -------------------------------
+        float wacc[3][4][4];
 #pragma unroll
-            for (int kk = 0; kk < kChunk / 2; kk += 8) {     // 16 rows = 8 words per k-step
-                uint32_t af[SA][4];
-                const int r0 = wm + gid, r1 = wm + gid + 8;
+        for (int l = 0; l < 3; ++l)
 #pragma unroll
-                for (int s = 0; s < SA; ++s) {
-                    af[s][0] = As[s * SW + swz(r0, kk + tig)];
-                    af[s][1] = As[s * SW + swz(r1, kk + tig)];
-                    af[s][2] = As[s * SW + swz(r0, kk + 4 + tig)];
-                    af[s][3] = As[s * SW + swz(r1, kk + 4 + tig)];
-                }
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int j = 0; j < kNT; ++j) {
-                    const int n = wn + 8 * j + gid;
-                    uint32_t bf[SB][2];
+                for (int v = 0; v < 4; ++v) wacc[l][j][v] = 0.f;
+        const int am = wm + (lane & 15);
+        const int bn = wn + (lane & 7) + ((lane >> 4) << 3);
 #pragma unroll
-                    for (int t = 0; t < SB; ++t) {
-                        bf[t][0] = Bs[t * SW + swz(n, kk + tig)];
-                        bf[t][1] = Bs[t * SW + swz(n, kk + 4 + tig)];
+        for (int ks = 0; ks < KW / 16; ++ks) {
+            uint32_t af[SA][4];
+#pragma unroll
+            for (int s = 0; s < SA; ++s) ldsm_x4(af[s], As_s + s * SLICE + chunk_off<KW>(am, 2 * ks + (lane >> 4)));
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {                 // pairs of n8 tiles
+                const unsigned boff = chunk_off<KW>(bn + 16 * p, 2 * ks + ((lane >> 3) & 1));
+#pragma unroll
+                for (int t = 1; t <= SB; ++t) {            // one B slice at a time
+                    uint32_t bf[4];
+                    ldsm_x4(bf, Bs_s + (t - 1) * SLICE + boff);
+#pragma unroll
+                    for (int s = 1; s <= SA; ++s) {
+                        const int L = s + t;
+                        if (L > LMAX) continue;
+                        const int cls = L == 2 ? 0 : (L == 3 ? 1 : 2);
+                        mma_bf16(wacc[cls][2 * p], af[s - 1], bf[0], bf[1]);
+                        mma_bf16(wacc[cls][2 * p + 1], af[s - 1], bf[2], bf[3]);
                     }
-#pragma unroll
-                    for (int s = 1; s <= SA; ++s)
-#pragma unroll
-                        for (int t = 1; t <= SB; ++t) {
-                            const int L = s + t;
-                            if (L > LMAX) continue;
-                            mma_bf16(wacc[L - 2][j], af[s - 1], bf[t - 1][0], bf[t - 1][1]);
-                        }
                 }
             }
         }
-        since_flush += kChunk;
-        if (since_flush >= kFlushRows) {
+        // ---- flush: exact window value into the int64 accumulators -----------
+        int dRa[2], dWa[2];
 #pragma unroll
-            for (int j = 0; j < kNT; ++j)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-#pragma unroll
-                    for (int l = 0; l < NLEV; ++l) {
-                        acc[j][v] += (long long)__float2int_rn(wacc[l][j][v]) << (8 * (NLEV - 1 - l));
-                        wacc[l][j][v] = 0.f;
-                    }
-                }
-            since_flush = 0;
+        for (int h = 0; h < 2; ++h) {
+            dRa[h] = sDR[0][wm + gid + 8 * h];
+            dWa[h] = sDW[0][wm + gid + 8 * h];
         }
-        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int n = wn + 8 * j + 2 * tig + (v & 1);
+                const int h = v >> 1;
+                const long long i2 = __float2int_rn(wacc[0][j][v] * pow2f(16));
+                const long long i3 = __float2int_rn(wacc[1][j][v] * pow2f(24));
+                const long long iR = __float2ll_rn(wacc[2][j][v] * pow2f(8 * LMAX));
+                const long long t = (i2 << (8 * (LMAX - 2))) + (i3 << (8 * (LMAX - 3))) + iR;
+                const int shR = min(dRa[h] + sDR[bo][n], 63), shW = min(dWa[h] + sDW[bo][n], 63);
+                acc[j][v] = (acc[j][v] >> shR) + (t >> shW);
+            }
     }
     if (!wact) return;
 
-    // ---- epilogue: levels -> int64 -> FP64, one atomic per element ----------
+    // ---- epilogue: int64 -> FP64, one atomic per element --------------------
 #pragma unroll
-    for (int j = 0; j < kNT; ++j)
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int m = wm + gid + (v >= 2 ? 8 : 0);
             const int n = wn + 8 * j + tig * 2 + (v & 1);
             const int gm = sGcolA[m], gn = sGcolB[n];
             if (gm < 0 || gn < 0) continue;
-            if (SYM && mi == ni && m > n) continue;      // lower half of a diagonal tile: mirrored below
-            long long t = acc[j][v];
-#pragma unroll
-            for (int l = 0; l < NLEV; ++l) t += (long long)__float2int_rn(wacc[l][j][v]) << (8 * (NLEV - 1 - l));
-            const double val = i64_scaled_to_double(t, sEa[m] + sEb[n] - 8 * LMAX);
+            if (diag && m > n) continue;                 // lower half of a diagonal tile: mirrored below
+            const int Ra = sR[0][m], Rb = sR[bo][n];
+            if (Ra == kNone || Rb == kNone) continue;
+            const double val = i64_scaled_to_double(acc[j][v], Ra + Rb - 8 * LMAX);
             if (val == 0.0) continue;
             atomicAdd(&g.G[(int64_t)gm * g.n_cols + gn], val);
             if (SYM && gm != gn) atomicAdd(&g.G[(int64_t)gn * g.n_cols + gm], val);
         }
 }
 
+template <int SA, int SB, int LMAX, bool SYM, int KW>
+cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
+    constexpr size_t smem = (size_t)(SA + SB) * kST * KW * 2;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, SYM, KW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    gram_tc_kernel<SA, SB, LMAX, SYM, KW><<<(unsigned)g.n_items, kThreads, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_gram_tc(const GramTcArgs& g, bool sym, cudaStream_t s) {
     if (g.n_items == 0) return cudaSuccess;
-    // The error is set by the residual after the last slice (|r| <= 2^(-8S-1)
-    // of the column bound) and by the first dropped level (<= 2^(-8 LMAX + 14)
-    // per product), so LMAX = S + 1 balances the two.  P^T Y: 3 slices, levels
-    // <= 4 (6 products, ~2^-25 of the result); P^T P: 5 slices, levels <= 6
-    // (15 products, ~2^-40: columns whose values span many binades within a
-    // group, as orbitals decaying across a p = 4 patch do, stay well inside
-    // a 1e-10 normwise bound).
-    if (sym)
-        gram_tc_kernel<5, 5, 6, true><<<(unsigned)g.n_items, kThreads, 0, s>>>(g);
-    else
-        gram_tc_kernel<3, 3, 4, false><<<(unsigned)g.n_items, kThreads, 0, s>>>(g);
-    return cudaGetLastError();
+    // P^T Y: 3 slices, levels <= 4, windows of 128 rows (the level-2 and
+    // level-3 window sums stay below 2^23); P^T P: 5 slices, levels <= 6,
+    // windows of 64 rows (shared memory for 10 staged slices).
+    if (sym) return launch_tc<5, 5, 6, true, 64>(g, s);
+    return launch_tc<3, 3, 4, false, 128>(g, s);
 }
 
-int gram_tc_tile() { return kTile; }
+int gram_tc_tile() { return kST; }
+int gram_tc_split_rows() { return 1024; }
 
 }  // namespace femf

@@ -762,11 +762,14 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                 if (width > 0) {
                     const int gidx = (int)b->tc_groups.size();
                     const int nt = (width + gram_tc_tile() - 1) / gram_tc_tile();
+                    const int split = gram_tc_split_rows();
                     for (int mi = 0; mi < nt; ++mi)
-                        for (int ni = 0; ni < nt; ++ni) {
-                            b->tc_py.push_back(GramTcItem{gidx, mi | (ni << 16)});
-                            if (mi <= ni) b->tc_pp.push_back(GramTcItem{gidx, mi | (ni << 16)});
-                        }
+                        for (int ni = 0; ni < nt; ++ni)
+                            for (int k0 = 0; k0 < gr.k_rows; k0 += split) {
+                                const GramTcItem item{gidx, mi | (ni << 16), k0, std::min(gr.k_rows, k0 + split)};
+                                b->tc_py.push_back(item);
+                                if (mi <= ni) b->tc_pp.push_back(item);
+                            }
                     b->tc_groups.push_back(gr);
                 }
                 r = r1;
