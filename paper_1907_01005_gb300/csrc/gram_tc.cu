@@ -97,46 +97,76 @@ __device__ __forceinline__ unsigned chunk_off(int c, int kc) {
     return (unsigned)(c * (KW * 2) + ((kc ^ (c & 7)) << 4));
 }
 
-// Per-window state of one operand's 64 columns.
-struct ColState {
-    int* R;        // running reference exponent
-    int* dR;       // growth of R in this window (accumulator right shift)
-    int* dW;       // R - E(w) (window value right shift), 63 for an empty column
-    float* f1;     // 2^-(E>>1)   } x 2^-E = (x * f1) * f2 without underflow
-    float* f2;     // 2^-(E-(E>>1))
-};
-
-// Loads a window of one operand into registers: thread (column c, segment
-// seg) holds rows row0 .. row0+SEG-1 of column c; returns max |x|.
+// Loads rows kstart .. kstart+SEG-1 of the group (those at or past kend
+// read as zero) of one union column into registers and returns max |x|.
+// Consecutive rows of a row block are ld elements apart.  A segment that
+// touches at most two row blocks (always for p >= 2, whose row blocks hold
+// at least (2p)^3 >= SEG rows) gets its addresses from two bases, so all
+// loads are independent; otherwise the rows are walked one by one.
 template <int SEG>
 __device__ __forceinline__ float load_window(const float* __restrict__ X, int ci, const int64_t* sOff, int n_u,
-                                             const int* sRowRb, const int* sRowLoc, int row0, float (&v)[SEG]) {
-    float mx = 0.f;
-    const int slot = ci >> 16, a = (ci >> 8) & 0xff, ld = ci & 0xff;
+                                             const int* sPref, int nrb, int kstart, int kend, float (&v)[SEG]) {
 #pragma unroll
-    for (int i = 0; i < SEG; ++i) {
-        v[i] = 0.f;
-        const int r = sRowRb[row0 + i];
-        if (ci >= 0 && r >= 0) {
-            const int64_t o = sOff[r * n_u + slot];
-            if (o >= 0) v[i] = __ldg(X + o + (int64_t)sRowLoc[row0 + i] * ld + a);
+    for (int i = 0; i < SEG; ++i) v[i] = 0.f;
+    if (ci < 0 || kstart >= kend) return 0.f;
+    const int slot = ci >> 16, a = (ci >> 8) & 0xff, ld = ci & 0xff;
+    int r = 0;
+    while (r < nrb - 1 && kstart >= sPref[r + 1]) ++r;
+    const int end_r = sPref[r + 1];
+    float mx = 0.f;
+    if (r + 1 >= nrb || sPref[r + 2] >= kstart + SEG) {
+        const int64_t o0 = sOff[r * n_u + slot];
+        const int64_t o1 = r + 1 < nrb ? sOff[(r + 1) * n_u + slot] : -1;
+        const int64_t b0 = o0 + (int64_t)(kstart - sPref[r]) * ld + a;   // row kstart + i -> b0 + i ld
+        const int64_t b1 = o1 + a - (int64_t)end_r * ld;                  // row k >= end_r -> b1 + k ld
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) {
+            const int k = kstart + i;
+            const bool in0 = k < end_r;
+            const bool ok = k < kend && (in0 ? o0 >= 0 : o1 >= 0);
+            const int64_t ix = in0 ? b0 + (int64_t)i * ld : b1 + (int64_t)k * ld;
+            if (ok) v[i] = __ldg(X + ix);
         }
-        mx = fmaxf(mx, fabsf(v[i]));
+    } else {
+        int rr = r, e = end_r;
+        int64_t o = sOff[rr * n_u + slot];
+        int64_t idx = o + (int64_t)(kstart - sPref[rr]) * ld + a;
+        for (int i = 0; i < SEG; ++i) {
+            const int k = kstart + i;
+            if (k >= kend) break;
+            if (k == e) {                     // first row of the next row block (k < kend <= sPref[nrb])
+                ++rr;
+                e = sPref[rr + 1];
+                o = sOff[rr * n_u + slot];
+                idx = o + a;
+            }
+            if (o >= 0) v[i] = __ldg(X + idx);
+            idx += ld;
+        }
     }
+#pragma unroll
+    for (int i = 0; i < SEG; ++i) mx = fmaxf(mx, fabsf(v[i]));
     return mx;
 }
 
-// Column exponent of this window and the reference update.
-__device__ __forceinline__ void window_exponent(float mx, int c, const ColState& st) {
+// Column exponent of this window and the update of the running reference R
+// (kept in a register by each of the column's four staging lanes; the first
+// of them publishes the shifts for the flush and R for the epilogue).
+struct WinExp {
+    int dR, dW;       // accumulator shift (growth of R), window-value shift (R - E)
+    float f1, f2;     // x 2^-E = (x * f1) * f2 without underflow
+};
+__device__ __forceinline__ WinExp window_exponent(float mx, int& R) {
     const int E = mx > 0.f ? ilogbf(mx) + 1 : kNone;
-    const int R = st.R[c];
     const int newR = E > R ? E : R;
-    st.dR[c] = (R == kNone) ? 0 : min(newR - R, 63);
-    st.dW[c] = (E == kNone) ? 63 : min(newR - E, 63);
-    st.R[c] = newR;
+    WinExp w;
+    w.dR = (R == kNone) ? 0 : min(newR - R, 63);
+    w.dW = (E == kNone) ? 63 : min(newR - E, 63);
+    R = newR;
     const int e = (E == kNone) ? 0 : E;
-    st.f1[c] = pow2f(-(e >> 1));
-    st.f2[c] = pow2f(-(e - (e >> 1)));
+    w.f1 = pow2f(-(e >> 1));
+    w.f2 = pow2f(-(e - (e >> 1)));
+    return w;
 }
 
 // Slices a thread's SEG values (column c, rows seg*SEG ..) into S bf16
@@ -168,9 +198,43 @@ __device__ __forceinline__ void slice_store(unsigned char* base, int c, int seg,
     }
 }
 
-template <int SA, int SB, int LMAX, bool SYM, int KW>
+// Three slices with only the first on a fixed grid: y1 = q 2^-8 (|q| <= 256),
+// y2 = bf16(x - y1), y3 = bf16(x - y1 - y2).  Products y1 y1' stay on the
+// 2^-16 grid (exact window sums); the others are exact FP32 numbers whose
+// window sums are rounded, at a weight of 2^-8 of the result or less.
+template <int SEG, int KW>
+__device__ __forceinline__ void slice_store_nat(unsigned char* base, int c, int seg, float f1, float f2,
+                                                const float (&v)[SEG]) {
+    constexpr int SLICE = kST * KW * 2;
+#pragma unroll
+    for (int ch = 0; ch < SEG / 8; ++ch) {
+        const unsigned off = chunk_off<KW>(c, seg * (SEG / 8) + ch);
+        uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float r0 = (v[ch * 8 + 2 * i] * f1) * f2, r1 = (v[ch * 8 + 2 * i + 1] * f1) * f2;
+            const float q0 = rintf(r0 * 256.f), q1 = rintf(r1 * 256.f);
+            r0 = fmaf(-q0, 0.00390625f, r0);
+            r1 = fmaf(-q1, 0.00390625f, r1);
+            const __nv_bfloat162 b1 = __floats2bfloat162_rn(q0 * 0.00390625f, q1 * 0.00390625f);   // exact
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(r0, r1);
+            r0 -= __low2float(b2);
+            r1 -= __high2float(b2);
+            const __nv_bfloat162 b3 = __floats2bfloat162_rn(r0, r1);
+            w1[i] = *reinterpret_cast<const uint32_t*>(&b1);
+            w2[i] = *reinterpret_cast<const uint32_t*>(&b2);
+            w3[i] = *reinterpret_cast<const uint32_t*>(&b3);
+        }
+        *reinterpret_cast<uint4*>(base + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4*>(base + SLICE + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        *reinterpret_cast<uint4*>(base + 2 * SLICE + off) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+    }
+}
+
+template <int SA, int SB, int LMAX, bool SYM, int KW, bool NAT>
 __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g) {
     static_assert(KW % 32 == 0 && KW <= 128, "window rows");
+    static_assert(!NAT || (SA == 3 && SB == 3), "natural slices: three per operand");
     constexpr int SEG = KW / 4;                   // rows per staging thread
     constexpr int SLICE = kST * KW * 2;           // bytes per staged slice
     extern __shared__ __align__(128) unsigned char smem[];
@@ -178,11 +242,8 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
     unsigned char* Bs = smem + SA * SLICE;
     __shared__ int64_t sOff[kMaxGroup * kMaxUnion];
     __shared__ int sColA[kST], sColB[kST], sGcolA[kST], sGcolB[kST];
-    __shared__ int sRowRb[KW], sRowLoc[KW];
     __shared__ int sPref[kMaxGroup + 1];
-    __shared__ float sMax[2][4][kST];
     __shared__ int sR[2][kST], sDR[2][kST], sDW[2][kST];
-    __shared__ float sF1[2][kST], sF2[2][kST];
 
     const GramTcItem it = g.items[blockIdx.x];
     const GramTcGroup gr = g.groups[it.group];
@@ -209,21 +270,23 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
         sGcolA[tid] = ma < gr.width ? g.col_glob[gr.c_base + ma] : -1;
         sColB[tid] = nb < gr.width ? g.col_info[gr.c_base + nb] : -1;
         sGcolB[tid] = nb < gr.width ? g.col_glob[gr.c_base + nb] : -1;
-        sR[0][tid] = kNone;
-        sR[1][tid] = kNone;
     }
     if (tid == 0) {
         sPref[0] = 0;
         for (int r = 0; r < nrb; ++r) sPref[r + 1] = sPref[r] + g.rows[gr.r0 + r];
     }
+    __syncthreads();
+    if (sPref[nrb] != gr.k_rows) {                // the row walk relies on it
+        if (tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
+        return;
+    }
 
-    const ColState stA{sR[0], sDR[0], sDW[0], sF1[0], sF2[0]};
-    const ColState stB{sR[1], sDR[1], sDW[1], sF1[1], sF2[1]};
     const int bo = diag ? 0 : 1;                  // operand index of B's column state
     const int wm = (warp >> 1) * 16, wn = (warp & 1) * 32;
     const int gid = lane >> 2, tig = lane & 3;
     const bool wact = (mi * kST + wm < gr.width) && (ni * kST + wn < gr.width) && (!diag || wm < wn + 32);
-    const int c = tid & (kST - 1), seg = tid >> 6;
+    const int c = tid >> 2, seg = tid & 3;        // staging: a column's four row segments sit in one warp
+    int RA = kNone, RB = kNone;                   // running reference exponents of this thread's column
 
     long long acc[4][4];
 #pragma unroll
@@ -236,39 +299,45 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
 
     for (int k0 = it.k0; k0 < it.k1; k0 += KW) {
         __syncthreads();                           // tables ready; previous window's MMAs and flush done
-        if (tid < KW) {
-            const int k = k0 + tid;
-            int r = -1, loc = 0;
-            if (k < it.k1 && k < sPref[nrb]) {
-                r = 0;
-                while (r < nrb - 1 && k >= sPref[r + 1]) ++r;
-                loc = k - sPref[r];
+        // ---- per operand: load, column bound (4 lanes of a column), slices ----
+        {
+            const int ca = sColA[c];
+            float v[SEG];
+            float mx = load_window<SEG>(g.A, ca, sOff, gr.n_u, sPref, nrb, k0 + seg * SEG, it.k1, v);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            const WinExp e = window_exponent(mx, RA);
+            if (seg == 0) {
+                sDR[0][c] = e.dR;
+                sDW[0][c] = e.dW;
+                sR[0][c] = RA;
             }
-            sRowRb[tid] = r;
-            sRowLoc[tid] = loc;
+            if (ca >= 0) {
+                if constexpr (NAT) slice_store_nat<SEG, KW>(As, c, seg, e.f1, e.f2, v);
+                else slice_store<SA, SEG, KW>(As, c, seg, e.f1, e.f2, v);
+            }
         }
-        __syncthreads();
-        // ---- load the window, column bounds, exponents ----------------------
-        float va[SEG], vb[SEG];
-        sMax[0][seg][c] = load_window<SEG>(g.A, sColA[c], sOff, gr.n_u, sRowRb, sRowLoc, seg * SEG, va);
-        if (!diag) sMax[1][seg][c] = load_window<SEG>(g.B, sColB[c], sOff, gr.n_u, sRowRb, sRowLoc, seg * SEG, vb);
-        __syncthreads();
-        if (tid < kST) {
-            window_exponent(fmaxf(fmaxf(sMax[0][0][tid], sMax[0][1][tid]), fmaxf(sMax[0][2][tid], sMax[0][3][tid])),
-                            tid, stA);
-        } else if (tid < 2 * kST && !diag) {
-            const int cb = tid - kST;
-            window_exponent(fmaxf(fmaxf(sMax[1][0][cb], sMax[1][1][cb]), fmaxf(sMax[1][2][cb], sMax[1][3][cb])),
-                            cb, stB);
+        if (!diag) {
+            const int cb = sColB[c];
+            float v[SEG];
+            float mx = load_window<SEG>(g.B, cb, sOff, gr.n_u, sPref, nrb, k0 + seg * SEG, it.k1, v);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            const WinExp e = window_exponent(mx, RB);
+            if (seg == 0) {
+                sDR[1][c] = e.dR;
+                sDW[1][c] = e.dW;
+                sR[1][c] = RB;
+            }
+            if (cb >= 0) {
+                if constexpr (NAT) slice_store_nat<SEG, KW>(Bs, c, seg, e.f1, e.f2, v);
+                else slice_store<SB, SEG, KW>(Bs, c, seg, e.f1, e.f2, v);
+            }
         }
-        __syncthreads();
-        // ---- slices -----------------------------------------------------------
-        slice_store<SA, SEG, KW>(As, c, seg, sF1[0][c], sF2[0][c], va);
-        if (!diag) slice_store<SB, SEG, KW>(Bs, c, seg, sF1[1][c], sF2[1][c], vb);
         __syncthreads();
         if (!wact) continue;
 
-        // ---- tensor-core products of the window -------------------------------
+    // ---- tensor-core products of the window -------------------------------
         float wacc[3][4][4];
 #pragma unroll
         for (int l = 0; l < 3; ++l)
@@ -294,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
                     for (int s = 1; s <= SA; ++s) {
                         const int L = s + t;
                         if (L > LMAX) continue;
-                        const int cls = L == 2 ? 0 : (L == 3 ? 1 : 2);
+                        const int cls = L == 2 ? 0 : ((L == 3 && !NAT) ? 1 : 2);
                         mma_bf16(wacc[cls][2 * p], af[s - 1], bf[0], bf[1]);
                         mma_bf16(wacc[cls][2 * p + 1], af[s - 1], bf[2], bf[3]);
                     }
@@ -315,9 +384,9 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
                 const int n = wn + 8 * j + 2 * tig + (v & 1);
                 const int h = v >> 1;
                 const long long i2 = __float2int_rn(wacc[0][j][v] * pow2f(16));
-                const long long i3 = __float2int_rn(wacc[1][j][v] * pow2f(24));
                 const long long iR = __float2ll_rn(wacc[2][j][v] * pow2f(8 * LMAX));
-                const long long t = (i2 << (8 * (LMAX - 2))) + (i3 << (8 * (LMAX - 3))) + iR;
+                long long t = (i2 << (8 * (LMAX - 2))) + iR;
+                if constexpr (!NAT) t += (long long)__float2int_rn(wacc[1][j][v] * pow2f(24)) << (8 * (LMAX - 3));
                 const int shR = min(dRa[h] + sDR[bo][n], 63), shW = min(dWa[h] + sDW[bo][n], 63);
                 acc[j][v] = (acc[j][v] >> shR) + (t >> shW);
             }
@@ -343,17 +412,17 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
         }
 }
 
-template <int SA, int SB, int LMAX, bool SYM, int KW>
+template <int SA, int SB, int LMAX, bool SYM, int KW, bool NAT>
 cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
     constexpr size_t smem = (size_t)(SA + SB) * kST * KW * 2;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, SYM, KW>,
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, SYM, KW, NAT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    gram_tc_kernel<SA, SB, LMAX, SYM, KW><<<(unsigned)g.n_items, kThreads, smem, s>>>(g);
+    gram_tc_kernel<SA, SB, LMAX, SYM, KW, NAT><<<(unsigned)g.n_items, kThreads, smem, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -361,11 +430,12 @@ cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
 
 cudaError_t launch_gram_tc(const GramTcArgs& g, bool sym, cudaStream_t s) {
     if (g.n_items == 0) return cudaSuccess;
-    // P^T Y: 3 slices, levels <= 4, windows of 128 rows (the level-2 and
-    // level-3 window sums stay below 2^23); P^T P: 5 slices, levels <= 6,
-    // windows of 64 rows (shared memory for 10 staged slices).
-    if (sym) return launch_tc<5, 5, 6, true, 64>(g, s);
-    return launch_tc<3, 3, 4, false, 128>(g, s);
+    // P^T Y: 3 slices (the lower two natural bf16), levels <= 4, windows of
+    // 128 rows (the level-2 window sums stay below 2^23); P^T P: 5 slices on
+    // the fixed grid, levels <= 6, windows of 64 rows (shared memory for 10
+    // staged slices).
+    if (sym) return launch_tc<5, 5, 6, true, 64, false>(g, s);
+    return launch_tc<3, 3, 4, false, 128, true>(g, s);
 }
 
 int gram_tc_tile() { return kST; }
