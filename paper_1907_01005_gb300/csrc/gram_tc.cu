@@ -89,12 +89,24 @@ __device__ __forceinline__ double i64_scaled_to_double(long long t, int e2) {
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }   // |e| <= 126
 
 // Shared-memory byte offset of (column c, 16-byte chunk kc) in a slice of
-// kST columns x KW rows: chunks are XOR-swizzled by the column's low 3 bits
-// so that ldmatrix (8 columns, same chunk) and the staging stores hit 8
-// different bank groups.
+// kST columns x KW rows.  The low 3 bits of the chunk index are XOR-ed with
+// the column's low 3 bits (ldmatrix reads 8 consecutive columns at one
+// chunk) and with bit 3 of the chunk index moved to bit 1 (a staging store
+// phase writes 2 columns x 4 row segments, whose chunks differ in bits 2
+// and 3): both patterns hit 8 different 16-byte bank groups.
 template <int KW>
 __device__ __forceinline__ unsigned chunk_off(int c, int kc) {
-    return (unsigned)(c * (KW * 2) + ((kc ^ (c & 7)) << 4));
+    return (unsigned)(c * (KW * 2) + ((kc ^ (c & 7) ^ (((kc >> 3) & 1) << 1)) << 4));
+}
+
+// Rounds v 2^U (|v 2^U| < 2^62, v a float) to an int64 with two 32-bit
+// conversions (the 64-bit one runs on the FP64 pipe): the high part on the
+// 2^-H grid, then the exact remainder.
+template <int U, int H>
+__device__ __forceinline__ long long round_scaled_i64(float v) {
+    const float hi = rintf(v * pow2f(H));
+    const float rem = fmaf(-hi, pow2f(-H), v);               // exact
+    return ((long long)(int)hi << (U - H)) + (long long)__float2int_rn(rem * pow2f(U));
 }
 
 // Loads rows kstart .. kstart+SEG-1 of the group (those at or past kend
@@ -384,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
                 const int n = wn + 8 * j + 2 * tig + (v & 1);
                 const int h = v >> 1;
                 const long long i2 = __float2int_rn(wacc[0][j][v] * pow2f(16));
-                const long long iR = __float2ll_rn(wacc[2][j][v] * pow2f(8 * LMAX));
+                const long long iR = round_scaled_i64<8 * LMAX, 4 * LMAX>(wacc[2][j][v]);
                 long long t = (i2 << (8 * (LMAX - 2))) + iR;
                 if constexpr (!NAT) t += (long long)__float2int_rn(wacc[1][j][v] * pow2f(24)) << (8 * (LMAX - 3));
                 const int shR = min(dRa[h] + sDR[bo][n], 63), shW = min(dWa[h] + sDW[bo][n], 63);
