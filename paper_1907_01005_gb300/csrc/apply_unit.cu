@@ -3,47 +3,24 @@
 //
 // One CTA processes one packed work unit: a patch and up to four of its
 // column blocks (at most 32 columns, "lanes").  A thread owns one cell and
-// LPT lanes (two for FP32, one for FP64): it holds all (p+1)^3 nodal values
-// of its cell-columns in registers and applies the whole sum-factorised cell
-// operator there -- interpolation to the Gauss points along x, y, z, the
-// quadrature (three 1D Laplacian sweeps and the potential) and the
-// transposed interpolation.  In FP32 the two columns go through packed
-// FP32x2 FMAs, which halves the FMA instruction count.
+// one lane: it holds all (p+1)^3 nodal values of its cell-column in
+// registers and applies the whole sum-factorised cell operator there --
+// interpolation to the Gauss points along x, y, z, the quadrature (three 1D
+// Laplacian sweeps and the potential) and the transposed interpolation.
 //
 // Data movement works on 16-byte row chunks (block rows are padded to 16
 // bytes): the gather is a set of asynchronous 16-byte copies (cp.async, zero
 // fill for absent blocks and boundary nodes) into a per-block patch tensor
-// U_b[node][ld_b]; the cells add their results into a matching tensor with
-// shared-memory atomics; the scatter adds 16-byte chunks into Y with vector
-// reductions (red.global.add.v4.f32), 4x fewer than scalar atomics.
+// U_b[node][ld_b]; the cells add their results into a matching zeroed
+// tensor with shared-memory atomics; the scatter adds 16-byte chunks into Y
+// with vector reductions (red.global.add.v4.f32), 4x fewer than scalar
+// atomics.
 #include <algorithm>
 
 #include "fe_internal.h"
 
 namespace femf {
 namespace {
-
-// ---- lane arithmetic: packed FP32x2 FMA (sm_100+) or scalar FP64 -------
-template <typename T, int LPT>
-struct Lanes;
-template <>
-struct Lanes<float, 2> {       // two columns per thread, packed FP32x2 FMA
-    using V = float2;
-    static constexpr int n = 2;
-    __device__ static V zero() { return make_float2(0.f, 0.f); }
-    __device__ static V fma(float c, V a, V acc) { return __ffma2_rn(make_float2(c, c), a, acc); }
-    __device__ static V make(float x0, float x1) { return make_float2(x0, x1); }
-    __device__ static float get(V v, int i) { return i ? v.y : v.x; }
-};
-template <typename T>
-struct Lanes<T, 1> {           // one column per thread
-    using V = T;
-    static constexpr int n = 1;
-    __device__ static V zero() { return T(0); }
-    __device__ static V fma(T c, V a, V acc) { return ::fma(c, a, acc); }
-    __device__ static V make(T x0, T) { return x0; }
-    __device__ static T get(V v, int) { return v; }
-};
 
 // 16-byte chunk of one block row added into Y
 __device__ __forceinline__ void red_chunk(float* dst, const float* v) {
@@ -71,52 +48,40 @@ __device__ __forceinline__ int node_entry(int node, int px, int py, int pz, int 
     return ((dx + 2 * dy + 4 * dz) << 16) | row;
 }
 
-template <typename T, int P, int LPT_>
+template <typename T, int P>
 struct UnitGeo {
     static constexpr int N = P + 1, NP = 2 * P + 1, NPN = NP * NP * NP, N3 = N * N * N;
-    static constexpr int L = kUnitLanes, LPT = LPT_, TPC = L / LPT;   // threads per cell
-    static constexpr int THREADS = 8 * TPC;
+    static constexpr int L = kUnitLanes;             // columns of a unit, one per thread of a cell
+    static constexpr int THREADS = 8 * L;
     static constexpr int CH = 16 / sizeof(T);          // elements per 16-byte chunk
     static constexpr int MAXCH = kUnitLdSum / CH;      // chunks per node row of the unit
-    // one work area: it holds the gathered patch tensor U_b[node][ld_b], and
-    // after the cells have loaded their values into registers, the per-cell
-    // output slices Yc_b[cell][local node][ld_b]
-    static constexpr int TEN = (NPN > 8 * N3 ? NPN : 8 * N3) * kUnitLdSum;
-    static constexpr size_t bytes = (size_t)(TEN + 8 * N3) * sizeof(T);
+    static constexpr int TEN = NPN * kUnitLdSum;       // elements of one patch tensor (all blocks)
+    // gathered input U, accumulated output Yp, V at the Gauss points
+    static constexpr size_t bytes = (size_t)(2 * TEN + 8 * N3) * sizeof(T);
 };
 
-// resident CTAs per SM the register budget must allow: FP32 is bounded by
-// shared memory at 5-6 CTAs of 8 warps, FP64 at 2-3 (the persistent loop
-// otherwise lets the compiler keep loop-invariant values in registers and
-// trade two resident CTAs for them)
+// resident CTAs per SM the register budget must allow (a cell-column's
+// values and their sweep partner take 2 (p+1)^3 registers)
 template <typename T>
-constexpr int kUnitMinBlocks = sizeof(T) == 4 ? 5 : 2;
+constexpr int kUnitMinBlocks = sizeof(T) == 4 ? 4 : 2;
 
-template <typename T, int P, int LPT_>
-__global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T>)
+template <typename T, int P>
+__global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     apply_unit_kernel(const ApplyUnitArgs<T> a) {
-    using G = UnitGeo<T, P, LPT_>;
-    using LN = Lanes<T, LPT_>;
-    using V = typename LN::V;
-    constexpr int N = G::N, NP = G::NP, NPN = G::NPN, N3 = G::N3, L = G::L, LPT = G::LPT, TPC = G::TPC;
+    using G = UnitGeo<T, P>;
+    constexpr int N = G::N, NP = G::NP, NPN = G::NPN, N3 = G::N3, L = G::L;
     constexpr int CH = G::CH, MAXCH = G::MAXCH;
-    constexpr int SLOTS = MAXCH <= 16 ? 16 : 32;     // chunk slots per node (power of two)
-    constexpr int SHIFT = SLOTS == 16 ? 4 : 5;
-    static_assert(MAXCH <= SLOTS, "chunk slots");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* U = reinterpret_cast<T*>(smem_raw);         // per block b: [NPN][ld_b] at sBase[b]
-    T* Yc = U;                                     // per block b: [8][N3][ld_b] at sBaseY[b] (after the loads)
-    T* Vs = U + G::TEN;                            // [8][N3]  V at the Gauss points
+    T* Yp = U + G::TEN;                            // same layout, accumulated cell results
+    T* Vs = Yp + G::TEN;                           // [8][N3]  V at the Gauss points
     __shared__ int32_t sOff[kUnitBlocks][8];
-    __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sBaseY[kUnitBlocks], sLd[kUnitBlocks], sW[kUnitBlocks];
-    __shared__ unsigned short sList[NPN][8];       // (cell << 8) | local node, for the cells touching a node
-    __shared__ unsigned char sCnt[NPN];
-    __shared__ int sChB[SLOTS], sChC[SLOTS], sNch, sTen;
+    __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks], sW[kUnitBlocks];
+    __shared__ int sChB[MAXCH], sChC[MAXCH], sNch, sTen, sMagic;
     __shared__ int sNode[NPN];                     // (slot << 16) | row, or -1 on the boundary
-
     __shared__ int64_t sItem;
     const int tid = threadIdx.x;
-    constexpr int kElem16 = 16 / sizeof(T);      // elements per 16-byte offset unit
+    constexpr int kElem16 = 16 / sizeof(T);        // elements per 16-byte offset unit
     // One unit per CTA, or (persistent launch) units pulled from a ticket
     // counter until the list is exhausted.
     int64_t item = blockIdx.x;
@@ -159,42 +124,29 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T
         sOff[tid >> 3][tid & 7] = (tid >> 3) < unit.nb ? unit.off[tid >> 3][tid & 7] : -1;
     }
     if (tid == 0) {
-        int base = 0, basey = 0, nch = 0;
+        int base = 0, nch = 0;
         for (int q = 0; q < kUnitBlocks; ++q) {
             const int ldq = q < unit.nb ? unit.ld[q] : 0;
             sBase[q] = base;
-            sBaseY[q] = basey;
             sLd[q] = ldq;
             sW[q] = q < unit.nb ? unit.width[q] : 0;
             sMask[q] = q < unit.nb ? unit.cellmask[q] : 0;
             for (int c0 = 0; c0 < ldq; c0 += CH) { sChB[nch] = q; sChC[nch] = c0; ++nch; }
             base += NPN * ldq;
-            basey += 8 * N3 * ldq;
         }
         sNch = nch;
         sTen = base;
+        sMagic = (65536 + nch - 1) / nch;         // e / nch == (e * sMagic) >> 16 for e < NPN * nch
     }
-    for (int n = tid; n < NPN; n += blockDim.x) {
-        sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
-        const int i = n % NP, j = (n / NP) % NP, k = n / (NP * NP);
-        int c = 0;
-        for (int cz = 0; cz < 2; ++cz)
-            for (int cy = 0; cy < 2; ++cy)
-                for (int cx = 0; cx < 2; ++cx)
-                    if (k >= cz * P && k <= cz * P + P && j >= cy * P && j <= cy * P + P && i >= cx * P && i <= cx * P + P)
-                        sList[n][c++] = (unsigned short)(((cx + 2 * cy + 4 * cz) << 8) |
-                                                         (((k - cz * P) * N + (j - cy * P)) * N + (i - cx * P)));
-        sCnt[n] = (unsigned char)c;
-    }
+    for (int n = tid; n < NPN; n += blockDim.x) sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
     __syncthreads();
 
+    const int nch = sNch, magic = sMagic, ntask = NPN * nch;
     // ---- gather: asynchronous 16-byte copies of block row chunks ------------
     {
         const unsigned ubase = (unsigned)__cvta_generic_to_shared(U);
-        const int nch = sNch;
-        for (int e = tid; e < NPN * SLOTS; e += blockDim.x) {
-            const int node = e >> SHIFT, j = e & (SLOTS - 1);
-            if (j >= nch) continue;
+        for (int e = tid; e < ntask; e += blockDim.x) {
+            const int node = (e * magic) >> 16, j = e - node * nch;
             const int b = sChB[j], c0 = sChC[j], ld = sLd[b];
             const int ne = sNode[node];
             const int32_t o = ne >= 0 ? sOff[b][ne >> 16] : -1;
@@ -209,52 +161,41 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T
         const unsigned vbase = (unsigned)__cvta_generic_to_shared(Vs);
         for (int e = tid; e < 8 * N3 / CH; e += blockDim.x)
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(vbase + 16u * e), "l"(Vg + e * CH) : "memory");
+        // zero the output tensor while the copies are in flight
+        const int ten4 = sTen / CH;
+        for (int e = tid; e < ten4; e += blockDim.x) reinterpret_cast<uint4*>(Yp)[e] = make_uint4(0u, 0u, 0u, 0u);
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
     __syncthreads();
 
     // ---- cell operator in registers -----------------------------------------
     {
-        const int cell = tid / TPC, l0 = (tid % TPC) * LPT;
+        const int cell = tid / L, lane = tid % L;
         const int cx = cell & 1, cy = (cell >> 1) & 1, cz = (cell >> 2) & 1;
-        int lb[LPT], lofs[LPT], lld[LPT];
-        bool act = false;
-#pragma unroll
-        for (int h = 0; h < LPT; ++h) {
-            const int b = sLaneB[l0 + h];
-            lb[h] = b;
-            lld[h] = b >= 0 ? sLd[b] : 0;
-            lofs[h] = b >= 0 ? sBase[b] + sLaneA[l0 + h] : 0;
-            act |= b >= 0 && ((sMask[b] >> cell) & 1);
-        }
-        V u[N][N][N], t[N][N][N];
+        const int b = sLaneB[lane];
+        const bool act = b >= 0 && ((sMask[b] >> cell) & 1);
         if (act) {
+            const int ld = sLd[b];
+            // element of local node (z, y, x) of this cell in both patch tensors
+            const int base = sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * ld;
+            T u[N][N][N], t[N][N][N];
 #pragma unroll
             for (int z = 0; z < N; ++z)
 #pragma unroll
                 for (int y = 0; y < N; ++y)
 #pragma unroll
-                    for (int x = 0; x < N; ++x) {
-                        const int node = ((cz * P + z) * NP + (cy * P + y)) * NP + (cx * P + x);
-                        T v[LPT];
-#pragma unroll
-                        for (int h = 0; h < LPT; ++h) v[h] = lb[h] >= 0 ? U[lofs[h] + node * lld[h]] : T(0);
-                        u[z][y][x] = LN::make(v[0], v[LPT - 1]);
-                    }
-        }
-        __syncthreads();                                   // all inputs are in registers
-        if (act) {
+                    for (int x = 0; x < N; ++x) u[z][y][x] = U[base + ((z * NP + y) * NP + x) * ld];
             const auto& K = a.k;
-            // Sweeps run coefficient-outer: each (packed) coefficient is
-            // loaded once and applied to all N^2 lines of the sweep.
+            // Sweeps run coefficient-outer: each coefficient is applied to all
+            // N^2 lines of the sweep.
 #define SWEEP(C, IDX_D, IDX_S)                                               \
     _Pragma("unroll") for (int q = 0; q < N; ++q) {                          \
         _Pragma("unroll") for (int p2 = 0; p2 < N; ++p2) {                   \
             const T c = C[q][p2];                                            \
             _Pragma("unroll") for (int m = 0; m < N; ++m)                    \
             _Pragma("unroll") for (int n = 0; n < N; ++n) {                  \
-                V& d = IDX_D;                                                \
-                d = LN::fma(c, IDX_S, p2 == 0 ? LN::zero() : d);             \
+                T& d = IDX_D;                                                \
+                d = fma(c, IDX_S, p2 == 0 ? T(0) : d);                       \
             }                                                                \
         }                                                                    \
     }
@@ -271,7 +212,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T
 #pragma unroll
                 for (int y = 0; y < N; ++y)
 #pragma unroll
-                    for (int x = 0; x < N; ++x) u[z][y][x] = LN::fma(Vc[(z * N + y) * N + x], t[z][y][x], LN::zero());
+                    for (int x = 0; x < N; ++x) u[z][y][x] = Vc[(z * N + y) * N + x] * t[z][y][x];
 #pragma unroll
             for (int q = 0; q < N; ++q)
 #pragma unroll
@@ -281,9 +222,9 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T
                     for (int m = 0; m < N; ++m)
 #pragma unroll
                         for (int n = 0; n < N; ++n) {
-                            u[m][n][q] = LN::fma(c0, t[m][n][l], u[m][n][q]);
-                            u[m][q][n] = LN::fma(c1, t[m][l][n], u[m][q][n]);
-                            u[q][m][n] = LN::fma(c2, t[l][m][n], u[q][m][n]);
+                            u[m][n][q] = fma(c0, t[m][n][l], u[m][n][q]);
+                            u[m][q][n] = fma(c1, t[m][l][n], u[m][q][n]);
+                            u[q][m][n] = fma(c2, t[l][m][n], u[q][m][n]);
                         }
                 }
             // integrate: transposed interpolation along x (with |J|), y, z
@@ -291,61 +232,39 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T
             SWEEP(K.Sb, u[m][q][n], t[m][p2][n])
             SWEEP(K.Sb, t[q][m][n], u[p2][m][n])
 #undef SWEEP
-            // the cell's output slice
+            // add the cell's result into the patch tensor (nodes on faces,
+            // edges and the centre are shared with the neighbouring cells)
 #pragma unroll
-            for (int h = 0; h < LPT; ++h) {
-                if (lb[h] < 0) continue;
-                T* dst = Yc + sBaseY[lb[h]] + (cell * N3) * lld[h] + sLaneA[l0 + h];
+            for (int z = 0; z < N; ++z)
 #pragma unroll
-                for (int z = 0; z < N; ++z)
+                for (int y = 0; y < N; ++y)
 #pragma unroll
-                    for (int y = 0; y < N; ++y)
-#pragma unroll
-                        for (int x = 0; x < N; ++x) dst[((z * N + y) * N + x) * lld[h]] = LN::get(t[z][y][x], h);
-            }
+                    for (int x = 0; x < N; ++x) atomicAdd(&Yp[base + ((z * NP + y) * NP + x) * ld], t[z][y][x]);
         }
     }
     __syncthreads();
 
     // ---- scatter-add of 16-byte chunks (Alg. 6, write step) -----------------
-    {
-        const int nch = sNch;
-        for (int e = tid; e < NPN * SLOTS; e += blockDim.x) {
-            const int node = e >> SHIFT, j = e & (SLOTS - 1);
-            if (j >= nch) continue;
-            const int ne = sNode[node];
-            if (ne < 0) continue;
-            const int b = sChB[j], c0 = sChC[j], ld = sLd[b];
-            const int32_t o = sOff[b][ne >> 16];
-            if (o < 0) continue;
-            // sum the slices of the (active) cells that touch the node; the
-            // slices' padding columns hold stale data and are dropped
-            T v[CH];
-#pragma unroll
-            for (int q = 0; q < CH; ++q) v[q] = T(0);
-            const int cnt = sCnt[node], mask = sMask[b];
-            const T* yb = Yc + sBaseY[b] + c0;
-            for (int c = 0; c < cnt; ++c) {
-                const int ent = sList[node][c], cell = ent >> 8;
-                if (!((mask >> cell) & 1)) continue;
-                const T* src = yb + (cell * N3 + (ent & 0xff)) * ld;   // 16-byte aligned
-                if constexpr (CH == 4) {
-                    const float4 f = *reinterpret_cast<const float4*>(src);
-                    v[0] += f.x; v[1] += f.y; v[2] += f.z; v[3] += f.w;
-                } else {
-#pragma unroll
-                    for (int q = 0; q < CH; ++q) v[q] += src[q];
-                }
-            }
-            const int w = sW[b];
-            bool nz = false;
-#pragma unroll
-            for (int q = 0; q < CH; ++q) {
-                if (c0 + q >= w) v[q] = T(0);
-                nz |= v[q] != T(0);
-            }
-            if (nz) red_chunk(a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld + c0, v);
+    for (int e = tid; e < ntask; e += blockDim.x) {
+        const int node = (e * magic) >> 16, j = e - node * nch;
+        const int ne = sNode[node];
+        if (ne < 0) continue;
+        const int b = sChB[j];
+        const int32_t o = sOff[b][ne >> 16];
+        if (o < 0) continue;
+        const int c0 = sChC[j], ld = sLd[b];
+        T v[CH];
+        if constexpr (CH == 4) {
+            const float4 f = *reinterpret_cast<const float4*>(Yp + sBase[b] + node * ld + c0);
+            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+        } else {
+            const double2 f = *reinterpret_cast<const double2*>(Yp + sBase[b] + node * ld + c0);
+            v[0] = f.x; v[1] = f.y;
         }
+        bool nz = false;
+#pragma unroll
+        for (int q = 0; q < CH; ++q) nz |= v[q] != T(0);
+        if (nz) red_chunk(a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld + c0, v);
     }
     }  // unit_ok
     if (!a.ticket) break;
@@ -356,14 +275,14 @@ __global__ void __launch_bounds__(UnitGeo<T, P, LPT_>::THREADS, kUnitMinBlocks<T
     }
 }
 
-template <typename T, int P, int LPT>
+template <typename T, int P>
 cudaError_t launch_units_p(const ApplyUnitArgs<T>& a, cudaStream_t s) {
-    using G = UnitGeo<T, P, LPT>;
+    using G = UnitGeo<T, P>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(apply_unit_kernel<T, P, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes);
+        cudaError_t e = cudaFuncSetAttribute(apply_unit_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(apply_unit_kernel<T, P, LPT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(apply_unit_kernel<T, P>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -375,22 +294,17 @@ cudaError_t launch_units_p(const ApplyUnitArgs<T>& a, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = (unsigned)std::min<int64_t>(a.n_units, (int64_t)sms * std::max(1, a.ctas_per_sm));
     }
-    apply_unit_kernel<T, P, LPT><<<grid, G::THREADS, G::bytes, s>>>(a);
+    apply_unit_kernel<T, P><<<grid, G::THREADS, G::bytes, s>>>(a);
     return cudaGetLastError();
 }
-
-// columns per thread: FP32 runs one column per thread (more warps to hide the
-// gather latency); FP64 one column per thread
-template <typename T>
-constexpr int kLanesPerThread = 1;
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_apply_units(int p, const ApplyUnitArgs<T>& a, cudaStream_t s) {
     switch (p) {
-        case 1: return launch_units_p<T, 1, kLanesPerThread<T>>(a, s);
-        case 2: return launch_units_p<T, 2, kLanesPerThread<T>>(a, s);
+        case 1: return launch_units_p<T, 1>(a, s);
+        case 2: return launch_units_p<T, 2>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
