@@ -21,6 +21,8 @@ import tempfile
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -39,6 +41,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--serving", type=int, default=200, help="requests in the serving run (0: skip)")
+    ap.add_argument("--serving-pool", type=int, default=8, help="distinct workloads in the serving mix")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="draw serving meshes up to 64x40x40 and 640 orbitals (slow host set-up)")
     ap.add_argument("--cpu-blocks", type=int, default=8, help="column blocks in the CPU oracle sample")
     return ap.parse_args()
 
@@ -289,6 +295,49 @@ def time_graph(pb, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def serving_run(args):
+    """Poisson stream of apply_H + Gram requests through the continuous-batching
+    server: a pool of distinct workloads drawn from the serving mix, arrivals
+    at 80% of the rate one request at a time would sustain."""
+    from paper_1907_01005_gb300 import harness
+    from paper_1907_01005_gb300.serving import Server, latency_stats
+    from synth import inputs
+    meshes = inputs.SERVING_MESHES if args.serving_full else inputs.SERVING_MESHES[:2]
+    orbs = (32, 640) if args.serving_full else (32, 320)
+    t0 = time.perf_counter()
+    probs = []
+    for cfg in inputs.serving_mix(args.serving_pool, meshes=meshes, orb_range=orbs):
+        try:
+            probs.append(harness.build_problem(cfg, 1))
+        except Exception as e:           # a drawn pattern the library refuses (reported, not served)
+            print(f"serving: skipped {cfg.name}: {e}", file=sys.stderr)
+    setup_s = time.perf_counter() - t0
+    srv = Server(slots=4)
+    pids = [srv.register(pb) for pb in probs]
+    dofs_cols = {pid: srv.payloads[pid].dofs_cols for pid in pids}
+    for pid in pids:                      # residency and one warm call each
+        srv.submit(pid)
+        srv.drain()
+    t1 = time.perf_counter()
+    for pid in pids:
+        srv.submit(pid)
+        srv.drain()
+    serial = (time.perf_counter() - t1) / len(pids)
+    rate = 0.8 / serial
+    rng = np.random.default_rng(190701005)
+    arr = inputs.poisson_arrivals(args.serving, rate)
+    trace = [(float(arr[i]), int(pids[rng.integers(len(pids))])) for i in range(args.serving)]
+    srv.finished.clear()
+    reqs = srv.run_trace(trace)
+    st = latency_stats(reqs, dofs_cols)
+    st.update({"offered_rate_per_s": rate, "serial_ms": 1e3 * serial, "slots": srv.slots, "pool": len(pids),
+               "pool_dofs": [int(srv.payloads[p].problem.mesh.n_dofs) for p in pids],
+               "pool_columns": [int(srv.payloads[p].problem.n_cols) for p in pids],
+               "pool_degree": [int(srv.payloads[p].problem.cfg.p) for p in pids],
+               "evictions": srv.evictions, "host_setup_s": setup_s, "dtype": "f32"})
+    return st
+
+
 def pct(v, q):
     v = sorted(v)
     return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
@@ -441,6 +490,11 @@ def main():
                        "h2d_bytes_per_step": int(info.value_bytes),
                        "d2h_bytes_per_step": int(info.value_bytes + 2 * M * M * 8),
                        "ms_per_step": 1e3 * t_e2e}
+
+    if args.serving > 0:
+        pb = d = None                      # release the benchmark workload's device buffers
+        torch.cuda.empty_cache()
+        line["serving"] = serving_run(args)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(cfg, args.cpu_blocks)

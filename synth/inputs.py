@@ -240,3 +240,52 @@ def support_candidates(cfg: Config, alpha: int, centres: np.ndarray | None = Non
     callers can restrict the points they evaluate."""
     c = (orbital_centres(cfg) if centres is None else centres)[alpha]
     return c - cfg.radius, c + cfg.radius
+
+
+# ---------------------------------------------------------------------------
+# Serving request mix
+# ---------------------------------------------------------------------------
+SERVING_MESHES = ((16, 10, 10), (32, 20, 20), (64, 40, 40))
+
+
+def serving_config(index: int, mesh: tuple, p: int, n_orb: int, fill: float) -> Config:
+    """One serving request workload: a box of `mesh` cells of edge 1 for p = 2;
+    for p = 4 half as many cells per direction (rounded up to even) of edge
+    2, so both degrees cover about the same domain with the same DoF count),
+    `n_orb` uniform orbitals in column blocks of
+    about 8.4, and a support radius sized from the target block fill by a
+    ball-volume estimate (the actual fill is what the pattern builder finds).
+    """
+    h = 1.0 if p <= 2 else 2.0
+    nx, ny, nz = mesh
+    if p > 2:                                   # half the cells per direction, rounded up to even
+        nx, ny, nz = (2 * max(1, (n + 3) // 4) for n in (nx, ny, nz))
+    vol = nx * ny * nz * h ** 3
+    patch = 2.0 * h
+    r = (fill * vol * 3.0 / (4.0 * math.pi)) ** (1.0 / 3.0) - 2.0 * patch
+    r = max(r, 1.5 * h)
+    ncb = max(1, int(round(n_orb / 8.42)))
+    return Config(name=f"serve{index}", nx=nx, ny=ny, nz=nz, hx=h, hy=h, hz=h, p=p, n_orb=n_orb,
+                  n_col_blocks=ncb, radius=r, env_s2=(r / 1.75) ** 2, n_wells=max(4, nx * ny * nz // 2000),
+                  well_depth=1.0, well_sigma=2.0 * h, index=100 + index, target_fill=fill)
+
+
+def serving_mix(n: int, seed: int = SEED_BASE + 7, meshes=SERVING_MESHES, degrees=(2, 4),
+                orb_range=(32, 640), fill_range=(0.10, 0.30)):
+    """n request workloads drawn from the serving mix: mesh and degree
+    uniform over the given sets, orbital count log-uniform, fill uniform."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        mesh = meshes[int(rng.integers(len(meshes)))]
+        p = int(degrees[int(rng.integers(len(degrees)))])
+        m = int(round(math.exp(rng.uniform(math.log(orb_range[0]), math.log(orb_range[1])))))
+        f = float(rng.uniform(*fill_range))
+        out.append(serving_config(i, mesh, p, m, f))
+    return out
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int = SEED_BASE + 9) -> np.ndarray:
+    """Arrival offsets (s) of a Poisson stream of n requests."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
