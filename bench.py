@@ -52,13 +52,20 @@ def parse():
 # ---------------------------------------------------------------------------
 # distributed plumbing (replicas only: no data-path collective)
 # ---------------------------------------------------------------------------
-def dist_init(n):
+def dist_init(n, backend=None):
+    """Rank, world size and local rank from the torchrun environment; with
+    more than one rank, a process group (NCCL when CUDA is present, else
+    gloo) used only for the timing barrier and the max over ranks."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -73,57 +80,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-# ---------------------------------------------------------------------------
-# clocks during the timed region
-# ---------------------------------------------------------------------------
-class Clocks:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index):
-        self.idx = gpu_index
-        self.proc = None
-        fd, self.path = tempfile.mkstemp(prefix="fe_clocks_", suffix=".csv")
-        os.close(fd)
-
-    def start(self):
-        try:
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
-            self.proc = None
-
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        self.proc.wait()
-        self.f.close()
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "samples": len(sm), "reasons": sorted(reasons)}
+def whole_job_value(n_dofs, n_cols, ms_step, world):
+    """Weak scaling over replicas: every rank processes the same workload, so
+    the job processes world * N * M DoF-columns per (max over ranks) step."""
+    return world * n_dofs * n_cols / (ms_step * 1e-3)
 
 
 # ---------------------------------------------------------------------------
@@ -166,8 +132,7 @@ def oracle_sample(cfg, n_blocks, fp32=True):
 
 
 def run_reference(args):
-    rank, world, _ = dist_init(args.gpus)
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:      # rank 0 alone runs the oracle; others exit
         return
     from synth import inputs
     cfg = inputs.get_config(args.config)
@@ -378,7 +343,7 @@ def main():
         raise RuntimeError("device status word set during the timed region")
     graph_ms = time_graph(pb, args.steps, args.warmup)
     ms_step = max_over_ranks(total_ms / args.steps, world)
-    value = world * N * M / (ms_step * 1e-3)
+    value = whole_job_value(N, M, ms_step, world)
 
     # algorithmic work per launch (stored entries, not the 16-byte row padding):
     # apply reads P and V_q and writes Y; P^T Y reads P and Y; P^T P reads P
@@ -491,7 +456,7 @@ def main():
                        "d2h_bytes_per_step": int(info.value_bytes + 2 * M * M * 8),
                        "ms_per_step": 1e3 * t_e2e}
 
-    if args.serving > 0:
+    if args.serving > 0 and world == 1:
         pb = d = None                      # release the benchmark workload's device buffers
         torch.cuda.empty_cache()
         line["serving"] = serving_run(args)
