@@ -93,6 +93,54 @@ def whole_job_value(n_dofs, n_cols, ms_step, world):
 
 
 # ---------------------------------------------------------------------------
+# SM clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        fd, self.path = tempfile.mkstemp(prefix="fe_clocks_", suffix=".csv")
+        os.close(fd)
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
 def oracle_sample(cfg, n_blocks, fp32=True):
@@ -210,20 +258,27 @@ def probe_alu(dtype):
 
 
 def time_path(pb, steps, warmup):
-    """Per-step CUDA-event times (ms) of the three calls on the current stream."""
+    """CUDA-event times (ms) on the current stream: `steps` whole steps through
+    fe_apply_H_gram (P^T P overlapped with the apply), then `steps` runs of the
+    three calls one after another for the per-kernel breakdown."""
     import torch
-    from paper_1907_01005_gb300 import apply_H, gram_PtP, gram_PtY
+    from paper_1907_01005_gb300 import apply_H, apply_H_gram, gram_PtP, gram_PtY
     d = pb.dev
     s = torch.cuda.current_stream()
     for _ in range(warmup):
-        apply_H(pb.mesh, pb.P, pb.Y, s)
-        gram_PtY(pb.P, pb.Y, d["G_PY"], s)
-        gram_PtP(pb.P, d["G_PP"], s)
+        apply_H_gram(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], s)
     torch.cuda.synchronize()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
-    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(s)
     for k in range(steps):
-        e = ev[k]
+        apply_H_gram(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], s)
+        ev[k + 1].record(s)
+    torch.cuda.synchronize()
+    total = ev[0].elapsed_time(ev[-1])
+    per = {"step": [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]}
+    eb = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for k in range(steps):
+        e = eb[k]
         e[0].record(s)
         apply_H(pb.mesh, pb.P, pb.Y, s)
         e[1].record(s)
@@ -232,11 +287,10 @@ def time_path(pb, steps, warmup):
         gram_PtP(pb.P, d["G_PP"], s)
         e[3].record(s)
     torch.cuda.synchronize()
-    total = ev[0][0].elapsed_time(ev[-1][3])
-    per = {"apply": [e[0].elapsed_time(e[1]) for e in ev],
-           "gram_py": [e[1].elapsed_time(e[2]) for e in ev],
-           "gram_pp": [e[2].elapsed_time(e[3]) for e in ev],
-           "step": [e[0].elapsed_time(e[3]) for e in ev]}
+    per["apply"] = [e[0].elapsed_time(e[1]) for e in eb]
+    per["gram_py"] = [e[1].elapsed_time(e[2]) for e in eb]
+    per["gram_pp"] = [e[2].elapsed_time(e[3]) for e in eb]
+    per["sequential"] = [e[0].elapsed_time(e[3]) for e in eb]
     return total, per
 
 
@@ -413,6 +467,7 @@ def main():
                        "autotune_apply_ms": tune_ms},
             "graph_ms_per_step": graph_ms,
             "p50_ms": pct(per["step"], 0.5), "p99_ms": pct(per["step"], 0.99),
+            "sequential_ms_per_step": statistics.median(per["sequential"]),
             "apply_dof_cols_per_s": N * M / t_apply,
             "gram_gflops": {"PtY": info.gram_flops / t_py / 1e9, "PtP": info.gram_flops / t_pp / 1e9},
             "kernels": kernels, "roofline": roof, "step_hbm_roofline": step_roof,

@@ -230,7 +230,12 @@ int fe_gram_PtY(const fe_bcsr* P, const fe_bcsr* Y, double* G_dev, void* stream)
  * computed for column-block pairs c1 <= c2 and mirrored. */
 int fe_gram_PtP(const fe_bcsr* P, double* G_dev, void* stream);
 
-/* fe_apply_H, then fe_gram_PtY and fe_gram_PtP, on one stream. */
+/* fe_apply_H then fe_gram_PtY on `stream`, and fe_gram_PtP (which does not
+ * read Y) concurrently on a side stream owned by P, forked from `stream`
+ * before the apply and joined back after fe_gram_PtY with events; all work
+ * is ordered after earlier work on `stream` and before later work on it
+ * (stream capture of the call records the fork and the join).  The side
+ * stream is created on the first call and destroyed with P. */
 int fe_apply_H_gram(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_PY_dev,
                     double* G_PP_dev, void* stream);
 

@@ -198,7 +198,15 @@ struct fe_bcsr {
     uint64_t fingerprint = 0;
     void* values = nullptr;
     void* tables = nullptr;
+    // side stream of fe_apply_H_gram (P^T P runs beside the apply), created on first use
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t elem() const { return dtype == FE_F64 ? 8 : 4; }
+    ~fe_bcsr() {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
+    }
 };
 
 namespace {
@@ -1028,11 +1036,25 @@ int fe_gram_PtP(const fe_bcsr* P, double* G, void* stream) {
 }
 
 int fe_apply_H_gram(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY, double* G_PP, void* stream) {
-    int rc = fe_apply_H(m, P, Y, stream);
+    int rc = check_pair("fe_apply_H_gram", m, P, Y);
     if (rc) return rc;
-    rc = fe_gram_PtY(P, Y, G_PY, stream);
-    if (rc) return rc;
-    return fe_gram_PtP(P, G_PP, stream);
+    // P^T P does not depend on Y: it runs on P's side stream, forked from and
+    // joined back into `stream` with events (a pattern stream capture keeps)
+    fe_bcsr* Pm = const_cast<fe_bcsr*>(P);
+    if (!Pm->side) {
+        FE_TRY_CUDA(cudaStreamCreateWithFlags(&Pm->side, cudaStreamNonBlocking), "fe_apply_H_gram: side stream");
+        FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_fork, cudaEventDisableTiming), "fe_apply_H_gram: event");
+        FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_join, cudaEventDisableTiming), "fe_apply_H_gram: event");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    FE_TRY_CUDA(cudaEventRecord(Pm->ev_fork, s), "fe_apply_H_gram: fork");
+    FE_TRY_CUDA(cudaStreamWaitEvent(Pm->side, Pm->ev_fork, 0), "fe_apply_H_gram: fork");
+    const int rc_pp = fe_gram_PtP(P, G_PP, Pm->side);
+    FE_TRY_CUDA(cudaEventRecord(Pm->ev_join, Pm->side), "fe_apply_H_gram: join");
+    rc = fe_apply_H(m, P, Y, stream);
+    if (rc == FE_OK) rc = fe_gram_PtY(P, Y, G_PY, stream);
+    FE_TRY_CUDA(cudaStreamWaitEvent(s, Pm->ev_join, 0), "fe_apply_H_gram: join");
+    return rc != FE_OK ? rc : rc_pp;
 }
 
 int fe_apply_H_gram_host(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY, double* G_PP, const void* P_host,

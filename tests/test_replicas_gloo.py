@@ -56,3 +56,11 @@ def test_reference_arm_other_ranks_exit_quietly(capsys, monkeypatch):
         gpus, steps, warmup, config = 2, 1, 0, "tiny"
     assert bench.run_reference(A()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_bench_parses_and_clock_sampler_degrades_without_gpu():
+    import bench
+    c = bench.Clocks(0)
+    c.start()
+    res = c.stop()
+    assert "reasons" in res and "sm_mhz" in res
