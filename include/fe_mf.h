@@ -220,6 +220,14 @@ int fe_bcsr_bind(fe_bcsr* bcsr, void* values_dev, void* tables_dev, void* stream
  * the mesh uploaded and a potential of the same dtype registered (FE_ESTATE). */
 int fe_apply_H(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, void* stream);
 
+/* Y = mask(P) * (M P) with the mass matrix M_ij = sum_K int_K N_i N_j
+ * (Sec. 3.1, Eq. fe_matrices with the gradient term off and V = 1; Phi_M of
+ * Sec. 2, whose Gram product P^T Y = P^T M P is the overlap matrix of
+ * Eq. inner1).  Same kernels, layout, pattern rules and errors as
+ * fe_apply_H, except that no potential needs to be registered.  Use
+ * fe_gram_PtY(P, Y) for the overlap matrix. */
+int fe_apply_M(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, void* stream);
+
 /* G = P^T Y (Alg. 8, Eq. inner2): dense n_cols x n_cols FP64, row-major, in
  * the column order of the multivectors, zero where no row block holds both
  * column blocks.  G_dev is caller-owned device memory (n_cols^2 doubles);

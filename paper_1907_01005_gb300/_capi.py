@@ -80,6 +80,7 @@ SIGNATURES = {
     "fe_bcsr_row_strides": [_P, _P],
     "fe_bcsr_bind": [_P, _P, _P, _P],
     "fe_apply_H": [_P, _P, _P, _P],
+    "fe_apply_M": [_P, _P, _P, _P],
     "fe_gram_PtY": [_P, _P, _P, _P],
     "fe_gram_PtP": [_P, _P, _P],
     "fe_apply_H_gram": [_P, _P, _P, _P, _P, _P],

@@ -193,6 +193,11 @@ def apply_H(mesh: Mesh, P: BCSR, Y: BCSR, stream=None):
     check(capi.fe_apply_H(mesh.h, P.h, Y.h, _stream(stream)))
 
 
+def apply_M(mesh: Mesh, P: BCSR, Y: BCSR, stream=None):
+    """Y = mask(P) * (M P), the mass operator."""
+    check(capi.fe_apply_M(mesh.h, P.h, Y.h, _stream(stream)))
+
+
 def gram_PtY(P: BCSR, Y: BCSR, G, stream=None):
     check(capi.fe_gram_PtY(P.h, Y.h, _dptr(G), _stream(stream)))
 

@@ -60,7 +60,7 @@ __device__ __forceinline__ void atomic_add_shared(double* a, double v) { atomicA
 template <int P>
 constexpr int max_threads() { return (P >= 3 ? 4 : 8) * kMaxW * (P + 1); }
 
-template <typename T, int P>
+template <typename T, int P, bool MASS>
 __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const ApplyArgs<T> a) {
     using G = Geo<P>;
     constexpr int N = G::N, NP = G::NP, NPN = G::NPN, N3 = G::N3;
@@ -166,17 +166,20 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
                     for (int k = 0; k < N; ++k) s = fma(K.S[q][k], pa[k][i], s);
                     uq[q][i] = s;
                 }
-            // quadrature: x and z Laplacian terms and the potential
-            const T* V = a.Vq + ((int64_t)tile.patch * 8 + cell) * N3;
+            // quadrature: x and z Laplacian terms and the potential (the mass
+            // operator: |J| u_q only)
+            const T* V = MASS ? nullptr : a.Vq + ((int64_t)tile.patch * 8 + cell) * N3;
 #pragma unroll
             for (int kq = 0; kq < N; ++kq)
 #pragma unroll
                 for (int iq = 0; iq < N; ++iq) {
-                    T s = K.jxw * V[iq + N * (t + N * kq)] * uq[kq][iq];
+                    T s = MASS ? K.jxw * uq[kq][iq] : K.jxw * V[iq + N * (t + N * kq)] * uq[kq][iq];
+                    if constexpr (!MASS) {
 #pragma unroll
-                    for (int l = 0; l < N; ++l) s = fma(K.A[0][iq][l], uq[kq][l], s);
+                        for (int l = 0; l < N; ++l) s = fma(K.A[0][iq][l], uq[kq][l], s);
 #pragma unroll
-                    for (int l = 0; l < N; ++l) s = fma(K.A[2][kq][l], uq[l][iq], s);
+                        for (int l = 0; l < N; ++l) s = fma(K.A[2][kq][l], uq[l][iq], s);
+                    }
                     z1[kq][iq] = s;
                 }
         }
@@ -205,8 +208,10 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
 #pragma unroll
                 for (int i = 0; i < N; ++i) {
                     T s = pb[jq][i];
+                    if constexpr (!MASS) {
 #pragma unroll
-                    for (int l = 0; l < N; ++l) s = fma(K.A[1][jq][l], pa[l][i], s);
+                        for (int l = 0; l < N; ++l) s = fma(K.A[1][jq][l], pa[l][i], s);
+                    }
                     z1[jq][i] = s;
                 }
             // integrate along x then y: z1 -> pb -> pa  (nodal x, nodal y, q_z = t)
@@ -274,15 +279,21 @@ template <typename T, int P>
 cudaError_t launch_p(const ApplyArgs<T>& a, cudaStream_t s) {
     const size_t smem = apply_smem_bytes<T>(P, a.wmax, a.cells_per_round);
     const int threads = apply_threads<T>(P, a.wmax, a.cells_per_round);
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
-        cudaError_t e = cudaFuncSetAttribute(apply_plane_kernel<T, P>,
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(apply_plane_kernel<T, P, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(apply_plane_kernel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024);
         if (e != cudaSuccess) return e;
-        attr_set[sizeof(T) == 8] = true;
+        attr_set = true;
     }
     if (a.n_tiles == 0) return cudaSuccess;
-    apply_plane_kernel<T, P><<<(unsigned)a.n_tiles, threads, smem, s>>>(a);
+    if (a.mass)
+        apply_plane_kernel<T, P, true><<<(unsigned)a.n_tiles, threads, smem, s>>>(a);
+    else
+        apply_plane_kernel<T, P, false><<<(unsigned)a.n_tiles, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -65,7 +65,7 @@ struct UnitGeo {
 template <typename T>
 constexpr int kUnitMinBlocks = sizeof(T) == 4 ? 4 : 2;
 
-template <typename T, int P>
+template <typename T, int P, bool MASS>
 __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     apply_unit_kernel(const ApplyUnitArgs<T> a) {
     using G = UnitGeo<T, P>;
@@ -157,10 +157,13 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
                          "r"(ok ? 16 : 0) : "memory");
         }
         // the potential of the patch's cells (contiguous, 16-byte aligned)
-        const T* Vg = a.Vq + (int64_t)unit.patch * 8 * N3;
-        const unsigned vbase = (unsigned)__cvta_generic_to_shared(Vs);
-        for (int e = tid; e < 8 * N3 / CH; e += blockDim.x)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(vbase + 16u * e), "l"(Vg + e * CH) : "memory");
+        if constexpr (!MASS) {
+            const T* Vg = a.Vq + (int64_t)unit.patch * 8 * N3;
+            const unsigned vbase = (unsigned)__cvta_generic_to_shared(Vs);
+            for (int e = tid; e < 8 * N3 / CH; e += blockDim.x)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(vbase + 16u * e), "l"(Vg + e * CH)
+                             : "memory");
+        }
         // zero the output tensor while the copies are in flight
         const int ten4 = sTen / CH;
         for (int e = tid; e < ten4; e += blockDim.x) reinterpret_cast<uint4*>(Yp)[e] = make_uint4(0u, 0u, 0u, 0u);
@@ -205,16 +208,16 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
             SWEEP(K.S, t[q][m][n], u[p2][m][n])
             // quadrature: V u_q plus the three collocation Laplacian sweeps
             // (|J| is folded into the coefficients: A / |J| here, |J| Sb in the
-            // first transposed sweep below)
+            // first transposed sweep below); the mass operator keeps u_q
             const T* Vc = Vs + cell * N3;
 #pragma unroll
             for (int z = 0; z < N; ++z)
 #pragma unroll
                 for (int y = 0; y < N; ++y)
 #pragma unroll
-                    for (int x = 0; x < N; ++x) u[z][y][x] = Vc[(z * N + y) * N + x] * t[z][y][x];
+                    for (int x = 0; x < N; ++x) u[z][y][x] = MASS ? t[z][y][x] : Vc[(z * N + y) * N + x] * t[z][y][x];
 #pragma unroll
-            for (int q = 0; q < N; ++q)
+            for (int q = 0; q < (MASS ? 0 : N); ++q)
 #pragma unroll
                 for (int l = 0; l < N; ++l) {
                     const T c0 = K.A[0][q][l], c1 = K.A[1][q][l], c2 = K.A[2][q][l];
@@ -275,14 +278,22 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     }
 }
 
+template <typename T, int P, bool MASS>
+cudaError_t unit_attrs() {
+    using G = UnitGeo<T, P>;
+    cudaError_t e = cudaFuncSetAttribute(apply_unit_kernel<T, P, MASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(apply_unit_kernel<T, P, MASS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
 template <typename T, int P>
 cudaError_t launch_units_p(const ApplyUnitArgs<T>& a, cudaStream_t s) {
     using G = UnitGeo<T, P>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(apply_unit_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(apply_unit_kernel<T, P>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaError_t e = unit_attrs<T, P, false>();
+        if (e == cudaSuccess) e = unit_attrs<T, P, true>();
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -294,7 +305,10 @@ cudaError_t launch_units_p(const ApplyUnitArgs<T>& a, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = (unsigned)std::min<int64_t>(a.n_units, (int64_t)sms * std::max(1, a.ctas_per_sm));
     }
-    apply_unit_kernel<T, P><<<grid, G::THREADS, G::bytes, s>>>(a);
+    if (a.mass)
+        apply_unit_kernel<T, P, true><<<grid, G::THREADS, G::bytes, s>>>(a);
+    else
+        apply_unit_kernel<T, P, false><<<grid, G::THREADS, G::bytes, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -133,6 +133,7 @@ struct ApplyArgs {
     int32_t wmax;             // row stride of the patch tensors in shared memory
     int32_t cells_per_round;  // cells processed concurrently (1, 2, 4 or 8)
     int32_t* status;          // device status word (0 = ok)
+    int32_t mass;             // 1: the mass operator (no gradient term, V = 1; Vq unused)
     CellConsts<T> k;
 };
 
@@ -166,6 +167,7 @@ struct ApplyUnitArgs {
     int32_t lx, ly, lz;
     int32_t dirichlet;
     int32_t* status;
+    int32_t mass;                 // 1: the mass operator (no gradient term, V = 1; Vq unused)
     CellConsts<T> k;
 };
 template <typename T>

@@ -915,12 +915,13 @@ int choose_cells_per_round(int p, int wmax, int dtype, int& cpr) {
 }
 
 template <typename T>
-int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s) {
+int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool mass = false) {
     ApplyArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.P = static_cast<const T*>(P->values);
     a.Y = static_cast<T*>(Y->values);
-    a.Vq = static_cast<const T*>(m->vq[sizeof(T) == 8]);
+    a.Vq = mass ? nullptr : static_cast<const T*>(m->vq[sizeof(T) == 8]);
+    a.mass = mass ? 1 : 0;
     a.tiles = reinterpret_cast<const Tile*>(static_cast<const char*>(P->tables) + P->off_tiles);
     a.n_tiles = (int64_t)P->tiles.size();
     a.npx = m->np[0]; a.npy = m->np[1]; a.npz = m->np[2];
@@ -948,6 +949,7 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s) {
         }
         u.lx = a.lx; u.ly = a.ly; u.lz = a.lz; u.dirichlet = a.dirichlet;
         u.status = a.status;
+        u.mass = a.mass;
         u.k = a.k;
         // fold |J| into the coefficients so that the kernel uses the
         // potential as registered: Sb (|J| V + A) = (|J| Sb) (V + A / |J|),
@@ -1008,6 +1010,16 @@ int gram_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaStrea
 }  // namespace
 
 extern "C" {
+
+int fe_apply_M(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, void* stream) {
+    if (!m) return fail(FE_EINVAL, "fe_apply_M: mesh is NULL");
+    int rc = check_pair("fe_apply_M", m, P, Y);
+    if (rc) return rc;
+    if (!m->status) return fail(FE_ESTATE, "fe_apply_M: mesh is not uploaded");
+    if (m->p > kMaxP) return fail(FE_EUNSUPPORTED, "fe_apply_M: GPU kernels support p <= %d", kMaxP);
+    cudaStream_t s = (cudaStream_t)stream;
+    return P->dtype == FE_F64 ? apply_impl<double>(m, P, Y, s, true) : apply_impl<float>(m, P, Y, s, true);
+}
 
 int fe_apply_H(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, void* stream) {
     if (!m) return fail(FE_EINVAL, "fe_apply_H: mesh is NULL");
