@@ -51,6 +51,16 @@ __device__ __forceinline__ bool on_boundary(int I, int J, int K, int lx, int ly,
     return I == 0 || J == 0 || K == 0 || I == lx - 1 || J == ly - 1 || K == lz - 1;
 }
 
+// 16-byte chunk of one block row added into Y
+__device__ __forceinline__ void red_chunk(float* dst, const float* v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(dst), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3]) : "memory");
+}
+__device__ __forceinline__ void red_chunk(double* dst, const double* v) {
+    if (v[0] != 0.0) atomicAdd(dst, v[0]);
+    if (v[1] != 0.0) atomicAdd(dst + 1, v[1]);
+}
+
 __device__ __forceinline__ void atomic_add_shared(float* a, float v) { atomicAdd(a, v); }
 __device__ __forceinline__ void atomic_add_shared(double* a, double v) { atomicAdd(a, v); }
 
@@ -67,37 +77,50 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wmax = a.wmax;
     const int cpr = a.cells_per_round;
-    T* U = reinterpret_cast<T*>(smem_raw);          // [NPN][wmax] gathered input
-    T* Yp = U + NPN * wmax;                          // [NPN][wmax] accumulated output
-    T* exA = Yp + NPN * wmax;                        // [cpr*wmax][N3] exchange
+    const int ldmax = a.ldmax;
+    T* U = reinterpret_cast<T*>(smem_raw);          // [NPN][ld] gathered input (capacity NPN * ldmax)
+    T* Yp = U + NPN * ldmax;                         // [NPN][ld] accumulated output (16-byte aligned)
+    T* exA = Yp + NPN * ldmax;                       // [cpr*wmax][N3] exchange
     T* exB = exA + cpr * wmax * N3;
 
     const Tile& tile = a.tiles[blockIdx.x];
     const int w = tile.width, ld = tile.ld;
     const int px = tile.pxyz & 1023, py = (tile.pxyz >> 10) & 1023, pz = tile.pxyz >> 20;
     const int cellmask = tile.cellmask;
-    if (w > wmax || w < 1) {
+    if (w > wmax || w < 1 || ld < w || ld > ldmax || ld % (16 / (int)sizeof(T)) != 0 ||
+        ldmax % (16 / (int)sizeof(T)) != 0) {
         if (threadIdx.x == 0) atomicExch(a.status, kDevBadTile);
         return;
     }
-    int64_t off[8];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) off[b] = tile.off[b];
+    __shared__ int64_t sOff[8];
+    __shared__ int sNode[NPN];                       // (slot << 16) | row, or -1 (boundary / absent block)
+    if (threadIdx.x < 8) sOff[threadIdx.x] = tile.off[threadIdx.x];
+    __syncthreads();
+    for (int n = threadIdx.x; n < NPN; n += blockDim.x) {
+        const int i = n % NP, j = (n / NP) % NP, k = n / (NP * NP);
+        int slot, row;
+        node_slot_row<P>(i, j, k, px, py, pz, slot, row);
+        const bool bnd = a.dirichlet && on_boundary(2 * P * px + i, 2 * P * py + j, 2 * P * pz + k, a.lx, a.ly, a.lz);
+        sNode[n] = (bnd || sOff[slot] < 0) ? -1 : ((slot << 16) | row);
+    }
+    __syncthreads();
+    constexpr int CH = 16 / sizeof(T);               // elements per 16-byte chunk (ld is a multiple)
+    const int nch = ld / CH, ntask = NPN * nch;
 
-    // ---- gather (Alg. 6, read step) -------------------------------------
-    for (int e = threadIdx.x; e < NPN * wmax; e += blockDim.x) {
-        const int node = e / wmax, col = e - node * wmax;
-        T v = T(0);
-        if (col < w) {
-            const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
-            int slot, row;
-            node_slot_row<P>(i, j, k, px, py, pz, slot, row);
-            const bool bnd = a.dirichlet &&
-                on_boundary(2 * P * px + i, 2 * P * py + j, 2 * P * pz + k, a.lx, a.ly, a.lz);
-            if (off[slot] >= 0 && !bnd) v = a.P[off[slot] + (int64_t)row * ld + col];
+    // ---- gather (Alg. 6, read step): 16-byte asynchronous copies -------------
+    {
+        const unsigned ubase = (unsigned)__cvta_generic_to_shared(U);
+        for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
+            const int node = e / nch, q = e - node * nch;
+            const int ne = sNode[node];
+            const bool ok = ne >= 0;
+            const T* src = ok ? a.P + sOff[ne >> 16] + (int64_t)(ne & 0xffff) * ld + q * CH : a.P;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(ubase + (unsigned)((node * ld + q * CH) * sizeof(T))),
+                         "l"(src), "r"(ok ? 16 : 0) : "memory");
         }
-        U[e] = v;
-        Yp[e] = T(0);
+        for (int e = threadIdx.x; e < NPN * ld / CH; e += blockDim.x)
+            reinterpret_cast<uint4*>(Yp)[e] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
     __syncthreads();
 
@@ -122,7 +145,7 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
 #pragma unroll
                 for (int i = 0; i < N; ++i) {
                     const int node = (cx * P + i) + NP * ((cy * P + j) + NP * (cz * P + t));
-                    pa[j][i] = U[node * wmax + col];
+                    pa[j][i] = U[node * ld + col];
                 }
             // interpolate along x then y: pa -> pb -> pa  (values at (q_x, q_y, node z=t))
 #pragma unroll
@@ -256,36 +279,40 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
 #pragma unroll
                     for (int kq = 0; kq < N; ++kq) s = fma(K.Sb[ka][kq], pb[kq][ia], s);
                     const int node = (cx * P + ia) + NP * ((cy * P + t) + NP * (cz * P + ka));
-                    atomic_add_shared(&Yp[node * wmax + col], s);
+                    atomic_add_shared(&Yp[node * ld + col], s);
                 }
         }
         __syncthreads();
     }
 
-    // ---- scatter-add (Alg. 6, write step) ---------------------------------
-    for (int e = threadIdx.x; e < NPN * wmax; e += blockDim.x) {
-        const int node = e / wmax, c = e - node * wmax;
-        if (c >= w) continue;
-        const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
-        int slot, row;
-        node_slot_row<P>(i, j, k, px, py, pz, slot, row);
-        const bool bnd = a.dirichlet &&
-            on_boundary(2 * P * px + i, 2 * P * py + j, 2 * P * pz + k, a.lx, a.ly, a.lz);
-        if (off[slot] >= 0 && !bnd) atomicAdd(&a.Y[off[slot] + (int64_t)row * ld + c], Yp[e]);
+    // ---- scatter-add (Alg. 6, write step): 16-byte vector reductions ----------
+    for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
+        const int node = e / nch, q = e - node * nch;
+        const int ne = sNode[node];
+        if (ne < 0) continue;
+        T v[CH];
+        bool nz = false;
+#pragma unroll
+        for (int h = 0; h < CH; ++h) {
+            v[h] = Yp[node * ld + q * CH + h];          // padding columns stay zero
+            nz |= v[h] != T(0);
+        }
+        if (nz) red_chunk(a.Y + sOff[ne >> 16] + (int64_t)(ne & 0xffff) * ld + q * CH, v);
     }
 }
 
 template <typename T, int P>
 cudaError_t launch_p(const ApplyArgs<T>& a, cudaStream_t s) {
-    const size_t smem = apply_smem_bytes<T>(P, a.wmax, a.cells_per_round);
+    const size_t smem = apply_smem_bytes<T>(P, a.wmax, a.ldmax, a.cells_per_round);
     const int threads = apply_threads<T>(P, a.wmax, a.cells_per_round);
+    // dynamic shared memory up to 224 KB: the node tables take 3 KB of the 227 KB a CTA may use
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(apply_plane_kernel<T, P, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(apply_plane_kernel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     227 * 1024);
+                                     224 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -300,9 +327,9 @@ cudaError_t launch_p(const ApplyArgs<T>& a, cudaStream_t s) {
 }  // namespace
 
 template <typename T>
-size_t apply_smem_bytes(int p, int wmax, int cpr) {
+size_t apply_smem_bytes(int p, int wmax, int ldmax, int cpr) {
     const size_t np = 2 * p + 1, n = p + 1;
-    return (2 * np * np * np * wmax + 2 * (size_t)cpr * wmax * n * n * n) * sizeof(T);
+    return (2 * np * np * np * ldmax + 2 * (size_t)cpr * wmax * n * n * n) * sizeof(T);
 }
 
 int apply_max_threads(int p) {
@@ -333,8 +360,8 @@ cudaError_t launch_apply(int p, const ApplyArgs<T>& a, cudaStream_t s) {
 
 template cudaError_t launch_apply<float>(int, const ApplyArgs<float>&, cudaStream_t);
 template cudaError_t launch_apply<double>(int, const ApplyArgs<double>&, cudaStream_t);
-template size_t apply_smem_bytes<float>(int, int, int);
-template size_t apply_smem_bytes<double>(int, int, int);
+template size_t apply_smem_bytes<float>(int, int, int, int);
+template size_t apply_smem_bytes<double>(int, int, int, int);
 template int apply_threads<float>(int, int, int);
 template int apply_threads<double>(int, int, int);
 

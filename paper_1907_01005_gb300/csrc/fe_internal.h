@@ -130,7 +130,9 @@ struct ApplyArgs {
     int32_t npx, npy, npz;
     int32_t lx, ly, lz;
     int32_t dirichlet;
-    int32_t wmax;             // row stride of the patch tensors in shared memory
+    int32_t wmax;             // widest column block (columns per cell round)
+    int32_t ldmax;            // largest row stride (a multiple of 16 bytes): row stride capacity of
+                              // the patch tensors in shared memory
     int32_t cells_per_round;  // cells processed concurrently (1, 2, 4 or 8)
     int32_t* status;          // device status word (0 = ok)
     int32_t mass;             // 1: the mass operator (no gradient term, V = 1; Vq unused)
@@ -173,7 +175,7 @@ struct ApplyUnitArgs {
 template <typename T>
 cudaError_t launch_apply_units(int p, const ApplyUnitArgs<T>& a, cudaStream_t s);
 template <typename T>
-size_t apply_smem_bytes(int p, int wmax, int cells_per_round);
+size_t apply_smem_bytes(int p, int wmax, int ldmax, int cells_per_round);
 template <typename T>
 int apply_threads(int p, int wmax, int cells_per_round);
 int apply_max_threads(int p);

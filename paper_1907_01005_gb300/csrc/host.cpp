@@ -901,12 +901,13 @@ int check_pair(const char* fn, const fe_mesh* m, const fe_bcsr* P, const fe_bcsr
     return FE_OK;
 }
 
-int choose_cells_per_round(int p, int wmax, int dtype, int& cpr) {
+int choose_cells_per_round(int p, int wmax, int ldmax, int dtype, int& cpr) {
     const int candidates[4] = {8, 4, 2, 1};
     for (int c : candidates) {
-        const size_t smem = dtype == FE_F64 ? apply_smem_bytes<double>(p, wmax, c) : apply_smem_bytes<float>(p, wmax, c);
+        const size_t smem = dtype == FE_F64 ? apply_smem_bytes<double>(p, wmax, ldmax, c)
+                                            : apply_smem_bytes<float>(p, wmax, ldmax, c);
         const int thr = apply_threads<float>(p, wmax, c);
-        if (smem <= 227 * 1024 && thr <= apply_max_threads(p)) {
+        if (smem <= 224 * 1024 && thr <= apply_max_threads(p)) {   // 3 KB of static node tables
             cpr = c;
             return FE_OK;
         }
@@ -928,8 +929,9 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool ma
     a.lx = m->L[0]; a.ly = m->L[1]; a.lz = m->L[2];
     a.dirichlet = m->dirichlet;
     a.wmax = P->wmax;
+    a.ldmax = P->ld.empty() ? int(16 / sizeof(T)) : *std::max_element(P->ld.begin(), P->ld.end());
     int cpr = 8;
-    int rc = choose_cells_per_round(m->p, P->wmax, P->dtype, cpr);
+    int rc = choose_cells_per_round(m->p, P->wmax, a.ldmax, P->dtype, cpr);
     if (rc) return rc;
     if (P->cells_per_round > 0 && P->cells_per_round < cpr) cpr = P->cells_per_round;
     a.cells_per_round = cpr;
