@@ -206,6 +206,7 @@ int fe_bcsr_row_strides(const fe_bcsr* bcsr, int32_t* ld);
  * Gram work lists are copied on `stream` (tables_dev may be NULL for a
  * destination Y).  Both pointers are kept until re-bound or destroyed. */
 int fe_bcsr_bind(fe_bcsr* bcsr, void* values_dev, void* tables_dev, void* stream);
+/* (values_dev may be NULL when the pattern is empty: value_bytes = 0.) */
 
 /* ------------------------------------------------------------------------
  * Hot path (Alg. 6, Alg. 8)

@@ -850,7 +850,7 @@ int fe_bcsr_row_strides(const fe_bcsr* b, int32_t* ld) {
 }
 
 int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
-    if (!b || !values) return fail(FE_EINVAL, "fe_bcsr_bind: NULL argument");
+    if (!b || (!values && b->n_values > 0)) return fail(FE_EINVAL, "fe_bcsr_bind: NULL argument");
     if (reinterpret_cast<uintptr_t>(values) % 256 || (tables && reinterpret_cast<uintptr_t>(tables) % 256))
         return fail(FE_EINVAL, "fe_bcsr_bind: device buffers must be 256-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
@@ -896,8 +896,9 @@ int check_pair(const char* fn, const fe_mesh* m, const fe_bcsr* P, const fe_bcsr
     if (P->dtype != Y->dtype) return fail(FE_EPATTERN, "%s: P and Y have different dtypes", fn);
     if (P->fingerprint != Y->fingerprint || P->col_idx != Y->col_idx || P->cbp != Y->cbp)
         return fail(FE_EPATTERN, "%s: P and Y must have identical block patterns and column blocks", fn);
-    if (!P->values || !P->tables) return fail(FE_ESTATE, "%s: P is not bound with values and tables", fn);
-    if (!Y->values) return fail(FE_ESTATE, "%s: Y is not bound", fn);
+    // an empty pattern has no values: a NULL value array is then a valid binding
+    if ((!P->values && P->n_values > 0) || !P->tables) return fail(FE_ESTATE, "%s: P is not bound with values and tables", fn);
+    if (!Y->values && Y->n_values > 0) return fail(FE_ESTATE, "%s: Y is not bound", fn);
     return FE_OK;
 }
 
@@ -937,6 +938,7 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool ma
     a.cells_per_round = cpr;
     a.status = m->status;
     if constexpr (sizeof(T) == 8) a.k = m->kd; else a.k = m->kf;
+    if (Y->n_values == 0) return FE_OK;                       // empty pattern: nothing to compute
     FE_TRY_CUDA(cudaMemsetAsync(Y->values, 0, (size_t)Y->n_values * sizeof(T), s), "fe_apply_H: zero Y");
     if (m->p <= 2) {
         ApplyUnitArgs<T> u;
@@ -1044,7 +1046,8 @@ int fe_gram_PtY(const fe_bcsr* P, const fe_bcsr* Y, double* G, void* stream) {
 
 int fe_gram_PtP(const fe_bcsr* P, double* G, void* stream) {
     if (!P || !G) return fail(FE_EINVAL, "fe_gram_PtP: NULL argument");
-    if (!P->values || !P->tables) return fail(FE_ESTATE, "fe_gram_PtP: P is not bound with values and tables");
+    if ((!P->values && P->n_values > 0) || !P->tables)
+        return fail(FE_ESTATE, "fe_gram_PtP: P is not bound with values and tables");
     cudaStream_t s = (cudaStream_t)stream;
     return P->dtype == FE_F64 ? gram_impl<double>(P, P, true, G, s) : gram_impl<float>(P, P, true, G, s);
 }

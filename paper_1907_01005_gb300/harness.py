@@ -47,7 +47,10 @@ def _axis_coords(mesh: api.Mesh, xyz: np.ndarray, ijk: np.ndarray):
     return out
 
 
-def build_problem(cfg, dtype: int = FE_F32) -> Problem:
+def build_problem(cfg, dtype: int = FE_F32, pattern: str = "closed") -> Problem:
+    """pattern: "closed" (the library's closed pattern, Y = H P exactly) or
+    "support" (only the row blocks that hold support nodes of a column block,
+    so that Y = mask(P) * (H P) differs from H P)."""
     from synth import inputs
     mesh = api.Mesh(cfg.nx, cfg.ny, cfg.nz, cfg.hx, cfg.hy, cfg.hz, cfg.p, cfg.dirichlet)
     info = mesh.info
@@ -82,7 +85,16 @@ def build_problem(cfg, dtype: int = FE_F32) -> Problem:
             for c in range(ncb)]
     supp_ptr = np.concatenate([[0], np.cumsum([len(s) for s in supp])]).astype(np.int64)
     supp_dofs = np.concatenate(supp).astype(np.int64) if supp_ptr[-1] else np.zeros(1, np.int64)
-    row_ptr, col_idx = mesh.pattern_closed(ncb, supp_ptr, supp_dofs)
+    if pattern == "closed":
+        row_ptr, col_idx = mesh.pattern_closed(ncb, supp_ptr, supp_dofs)
+    else:
+        rbp = mesh.row_blocks()
+        R = mesh.n_row_blocks
+        has = np.zeros((R, ncb), bool)
+        for c in range(ncb):
+            has[np.searchsorted(rbp, supp[c], side="right") - 1, c] = True
+        row_ptr = np.concatenate([[0], np.cumsum(has.sum(1))]).astype(np.int64)
+        col_idx = np.nonzero(has)[1].astype(np.int32)
     P = api.BCSR(mesh, cbp, row_ptr, col_idx, dtype)
     Y = api.BCSR(mesh, cbp, row_ptr, col_idx, dtype)
     rb_ptr = mesh.row_blocks()

@@ -1,5 +1,6 @@
 """GPU parity at the paper-scale sizes (846,369 DoFs x 320 orbitals, p=2 and
-p=4), through the same fe_apply_H_gram call the benchmark times.
+p=4) and at the larger clustered workloads (1,686,177 DoFs x 640 orbitals),
+through the same fe_apply_H_gram call the benchmark times.
 
 The oracle cannot assemble and apply the whole operator quickly at this
 size, so Y is checked on sampled rows (each computed one by one from the
@@ -42,8 +43,8 @@ def _oracle_inputs(cfg, fp32):
     return mesh, blk, perm, ptr, mv, pat, cb_of_orb
 
 
-@pytest.mark.parametrize("dtype", [1, 2], ids=["f32", "f64"])
-@pytest.mark.parametrize("name", ["p2", "p4"])
+@pytest.mark.parametrize("name,dtype", [("p2", 1), ("p2", 2), ("p4", 1), ("p4", 2), ("large_p2", 1), ("large_p4", 1)],
+                         ids=["p2-f32", "p2-f64", "p4-f32", "p4-f64", "large_p2-f32", "large_p4-f32"])
 def test_paper_scale(name, dtype):
     cfg = inputs.get_config(name)
     fp32 = dtype == 1
