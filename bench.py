@@ -34,7 +34,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="p2")
     ap.add_argument("--no-fp64", action="store_true")
@@ -315,7 +315,7 @@ def time_graph(pb, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def serving_run(args):
+def serving_run(args, dtype=1):
     """Poisson stream of apply_H + Gram requests through the continuous-batching
     server: a pool of distinct workloads drawn from the serving mix, arrivals
     at 80% of the rate one request at a time would sustain."""
@@ -328,7 +328,7 @@ def serving_run(args):
     probs = []
     for cfg in inputs.serving_mix(args.serving_pool, meshes=meshes, orb_range=orbs):
         try:
-            probs.append(harness.build_problem(cfg, 1))
+            probs.append(harness.build_problem(cfg, dtype))
         except Exception as e:           # a drawn pattern the library refuses (reported, not served)
             print(f"serving: skipped {cfg.name}: {e}", file=sys.stderr)
     setup_s = time.perf_counter() - t0
@@ -354,7 +354,7 @@ def serving_run(args):
                "pool_dofs": [int(srv.payloads[p].problem.mesh.n_dofs) for p in pids],
                "pool_columns": [int(srv.payloads[p].problem.n_cols) for p in pids],
                "pool_degree": [int(srv.payloads[p].problem.cfg.p) for p in pids],
-               "evictions": srv.evictions, "host_setup_s": setup_s, "dtype": "f32"})
+               "evictions": srv.evictions, "host_setup_s": setup_s, "dtype": "f32" if dtype == 1 else "f64"})
     return st
 
 
@@ -515,7 +515,10 @@ def main():
     if args.serving > 0 and world == 1:
         pb = d = None                      # release the benchmark workload's device buffers
         torch.cuda.empty_cache()
-        line["serving"] = serving_run(args)
+        line["serving"] = serving_run(args, 1)
+        if not args.no_fp64:
+            torch.cuda.empty_cache()
+            line["serving_fp64"] = serving_run(args, 2)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(cfg, args.cpu_blocks)
