@@ -278,6 +278,17 @@ int fe_bcsr_set_launch(fe_bcsr* P, int32_t persistent, int32_t ctas_per_sm, int3
 int fe_bcsr_get_launch(const fe_bcsr* P, int32_t* persistent, int32_t* ctas_per_sm,
                        int32_t* cells_per_round);
 
+/* Declares (1) or withdraws (0, the default) that P's block pattern is closed
+ * for the values P will hold: every row block that owns a node of a cell
+ * touching the support of a column block is in that column block's pattern
+ * (fe_pattern_closed builds such patterns, Sec. 3.5 reading).  Then
+ * mask(P) * (H P) = H P, so P^T Y = P^T H P is symmetric, and fe_gram_PtY and
+ * fe_apply_H_gram compute its upper blocks only and mirror them.  Declaring
+ * it for a pattern that is not closed gives a wrong P^T Y.  FE_EINVAL for a
+ * flag other than 0 or 1. */
+int fe_bcsr_set_closed(fe_bcsr* P, int32_t closed);
+int fe_bcsr_get_closed(const fe_bcsr* P, int32_t* closed);
+
 /* CUDA graph of one fe_apply_H_gram step with the given (already bound)
  * buffers: runs the step once eagerly on `stream` (this sets kernel
  * attributes and checks the arguments), then captures it on a private stream

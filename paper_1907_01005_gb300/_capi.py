@@ -87,6 +87,8 @@ SIGNATURES = {
     "fe_apply_H_gram_host": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "fe_bcsr_set_launch": [_P, _i32, _i32, _i32],
     "fe_bcsr_get_launch": [_P, _pi32, _pi32, _pi32],
+    "fe_bcsr_set_closed": [_P, _i32],
+    "fe_bcsr_get_closed": [_P, _pi32],
     "fe_graph_create": [_P, _P, _P, _P, _P, _P, C.POINTER(_P)],
     "fe_graph_launch": [_P, _P],
     "fe_graph_destroy": [_P],

@@ -183,6 +183,15 @@ class BCSR:
     def set_launch(self, persistent: int, ctas_per_sm: int = 4, cells_per_round: int = 0):
         check(capi.fe_bcsr_set_launch(self.h, int(persistent), int(ctas_per_sm), int(cells_per_round)))
 
+    def set_closed(self, closed: bool):
+        """Declares the pattern closed for P's values (P^T Y is then symmetric)."""
+        check(capi.fe_bcsr_set_closed(self.h, 1 if closed else 0))
+
+    def get_closed(self) -> bool:
+        v = C.c_int32()
+        check(capi.fe_bcsr_get_closed(self.h, C.byref(v)))
+        return bool(v.value)
+
     def get_launch(self):
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         check(capi.fe_bcsr_get_launch(self.h, C.byref(a), C.byref(b), C.byref(c)))

@@ -116,7 +116,10 @@ struct GramTcArgs {
     double* G;
     int32_t* status;            // device status word (set on a malformed work item)
 };
-cudaError_t launch_gram_tc(const GramTcArgs& a, bool symmetric, cudaStream_t s);
+// PtY: full A^T B; PtP: A^T A on upper super-tiles, mirrored; PtYSym: A^T B
+// known to be symmetric (closed pattern), upper super-tiles, mirrored
+enum class GramMode { PtY = 0, PtP = 1, PtYSym = 2 };
+cudaError_t launch_gram_tc(const GramTcArgs& a, GramMode mode, cudaStream_t s);
 int gram_tc_tile();         // output super-tile edge of the tensor-core Gram
 int gram_tc_split_rows();   // rows per work item (multiple of every window height)
 

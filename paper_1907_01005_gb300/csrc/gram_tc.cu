@@ -243,7 +243,7 @@ __device__ __forceinline__ void slice_store_nat(unsigned char* base, int c, int 
     }
 }
 
-template <int SA, int SB, int LMAX, bool SYM, int KW, bool NAT>
+template <int SA, int SB, int LMAX, bool SYM, bool SAME, int KW, bool NAT>
 __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g) {
     static_assert(KW % 32 == 0 && KW <= 128, "window rows");
     static_assert(!NAT || (SA == 3 && SB == 3), "natural slices: three per operand");
@@ -272,7 +272,8 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
         if (tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
         return;
     }
-    const bool diag = SYM && mi == ni;            // B's columns are A's columns
+    const bool diag = SYM && mi == ni;            // diagonal super-tile of a symmetric product
+    const bool share = SAME && mi == ni;          // ... whose B columns are A's own (B = A)
 
     // ---- group tables ------------------------------------------------------
     for (int e = tid; e < nrb * gr.n_u; e += kThreads) sOff[e] = g.union_off[gr.u_base + e];
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
         return;
     }
 
-    const int bo = diag ? 0 : 1;                  // operand index of B's column state
+    const int bo = share ? 0 : 1;                 // operand index of B's column state
     const int wm = (warp >> 1) * 16, wn = (warp & 1) * 32;
     const int gid = lane >> 2, tig = lane & 3;
     const bool wact = (mi * kST + wm < gr.width) && (ni * kST + wn < gr.width) && (!diag || wm < wn + 32);
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
         for (int v = 0; v < 4; ++v) acc[j][v] = 0;
 
     const unsigned As_s = (unsigned)__cvta_generic_to_shared(As);
-    const unsigned Bs_s = (unsigned)__cvta_generic_to_shared(diag ? As : Bs);
+    const unsigned Bs_s = (unsigned)__cvta_generic_to_shared(share ? As : Bs);
 
     for (int k0 = it.k0; k0 < it.k1; k0 += KW) {
         __syncthreads();                           // tables ready; previous window's MMAs and flush done
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
                 else slice_store<SA, SEG, KW>(As, c, seg, e.f1, e.f2, v);
             }
         }
-        if (!diag) {
+        if (!share) {
             const int cb = sColB[c];
             float v[SEG];
             float mx = load_window<SEG>(g.B, cb, sOff, gr.n_u, sPref, nrb, k0 + seg * SEG, it.k1, v);
@@ -424,30 +425,34 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
         }
 }
 
-template <int SA, int SB, int LMAX, bool SYM, int KW, bool NAT>
+template <int SA, int SB, int LMAX, bool SYM, bool SAME, int KW, bool NAT>
 cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
     constexpr size_t smem = (size_t)(SA + SB) * kST * KW * 2;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, SYM, KW, NAT>,
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, SYM, SAME, KW, NAT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    gram_tc_kernel<SA, SB, LMAX, SYM, KW, NAT><<<(unsigned)g.n_items, kThreads, smem, s>>>(g);
+    gram_tc_kernel<SA, SB, LMAX, SYM, SAME, KW, NAT><<<(unsigned)g.n_items, kThreads, smem, s>>>(g);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_gram_tc(const GramTcArgs& g, bool sym, cudaStream_t s) {
+cudaError_t launch_gram_tc(const GramTcArgs& g, GramMode mode, cudaStream_t s) {
     if (g.n_items == 0) return cudaSuccess;
     // P^T Y: 3 slices (the lower two natural bf16), levels <= 4, windows of
     // 128 rows (the level-2 window sums stay below 2^23); P^T P: 5 slices on
     // the fixed grid, levels <= 6, windows of 64 rows (shared memory for 10
-    // staged slices).
-    if (sym) return launch_tc<5, 5, 6, true, 64, false>(g, s);
-    return launch_tc<3, 3, 4, false, 128, true>(g, s);
+    // staged slices).  The symmetric modes take the upper super-tiles only
+    // and mirror them.
+    switch (mode) {
+        case GramMode::PtP: return launch_tc<5, 5, 6, true, true, 64, false>(g, s);
+        case GramMode::PtYSym: return launch_tc<3, 3, 4, true, false, 128, true>(g, s);
+        default: return launch_tc<3, 3, 4, false, false, 128, true>(g, s);
+    }
 }
 
 int gram_tc_tile() { return kST; }

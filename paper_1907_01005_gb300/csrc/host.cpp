@@ -193,6 +193,7 @@ struct fe_bcsr {
     size_t off_units = 0, off_ld = 0, off_ticket = 0;
     // launch configuration of the apply (set by fe_bcsr_set_launch / fe_autotune)
     int32_t persistent = 0, ctas_per_sm = 4, cells_per_round = 0;
+    int32_t closed = 0;   // the caller declares the pattern closed for P's values (fe_bcsr_set_closed)
     int64_t active_cell_cols = 0;
     double gram_flops = 0.0;
     uint64_t fingerprint = 0;
@@ -987,7 +988,8 @@ int gram_tc_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaSt
     g.G = G;
     g.status = A->mesh ? A->mesh->status : nullptr;
     FE_TRY_CUDA(cudaMemsetAsync(G, 0, (size_t)A->n_cols * A->n_cols * sizeof(double), s), "gram: zero G");
-    FE_TRY_CUDA(launch_gram_tc(g, sym, s), "gram: tensor-core kernel launch");
+    const GramMode mode = !sym ? GramMode::PtY : (A == B ? GramMode::PtP : GramMode::PtYSym);
+    FE_TRY_CUDA(launch_gram_tc(g, mode, s), "gram: tensor-core kernel launch");
     return FE_OK;
 }
 
@@ -1041,7 +1043,9 @@ int fe_gram_PtY(const fe_bcsr* P, const fe_bcsr* Y, double* G, void* stream) {
     if (rc) return rc;
     if (!G) return fail(FE_EINVAL, "fe_gram_PtY: G is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    return P->dtype == FE_F64 ? gram_impl<double>(P, Y, false, G, s) : gram_impl<float>(P, Y, false, G, s);
+    // a closed pattern makes P^T Y = P^T H P symmetric: upper blocks, mirrored
+    const bool sym = P->closed != 0;
+    return P->dtype == FE_F64 ? gram_impl<double>(P, Y, sym, G, s) : gram_impl<float>(P, Y, sym, G, s);
 }
 
 int fe_gram_PtP(const fe_bcsr* P, double* G, void* stream) {
@@ -1127,6 +1131,18 @@ int fe_bcsr_set_launch(fe_bcsr* b, int32_t persistent, int32_t ctas_per_sm, int3
     b->persistent = persistent;
     b->ctas_per_sm = ctas_per_sm;
     b->cells_per_round = cells_per_round;
+    return FE_OK;
+}
+
+int fe_bcsr_set_closed(fe_bcsr* b, int32_t closed) {
+    if (!b || (closed != 0 && closed != 1)) return fail(FE_EINVAL, "fe_bcsr_set_closed: NULL multivector or flag not 0/1");
+    b->closed = closed;
+    return FE_OK;
+}
+
+int fe_bcsr_get_closed(const fe_bcsr* b, int32_t* closed) {
+    if (!b || !closed) return fail(FE_EINVAL, "fe_bcsr_get_closed: NULL argument");
+    *closed = b->closed;
     return FE_OK;
 }
 

@@ -97,6 +97,7 @@ def build_problem(cfg, dtype: int = FE_F32, pattern: str = "closed") -> Problem:
         col_idx = np.nonzero(has)[1].astype(np.int32)
     P = api.BCSR(mesh, cbp, row_ptr, col_idx, dtype)
     Y = api.BCSR(mesh, cbp, row_ptr, col_idx, dtype)
+    P.set_closed(pattern == "closed")   # the closed pattern is built from exactly these supports
     rb_ptr = mesh.row_blocks()
     offs = P.block_offsets()
     dense = np.full((mesh.n_row_blocks, ncb), -1, np.int64)

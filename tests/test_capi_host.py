@@ -183,3 +183,15 @@ def test_fp32_gram_union_limit(lib):
         BCSR(m, cbp, row_ptr, col_idx, 1)
     assert e.value.code == FE_EUNSUPPORTED
     assert BCSR(m, cbp, row_ptr, col_idx, 2).info.nnz_blocks == ncb
+
+
+def test_closed_flag(lib):
+    from paper_1907_01005_gb300 import BCSR, FeError, Mesh
+    m = Mesh(4, 4, 4, 1, 1, 1, 2)
+    R = m.n_row_blocks
+    b = BCSR(m, np.array([0, 8], np.int32), np.arange(R + 1, dtype=np.int64), np.zeros(R, np.int32), 1)
+    assert b.get_closed() is False
+    b.set_closed(True)
+    assert b.get_closed() is True
+    from paper_1907_01005_gb300 import _capi
+    assert _capi.fe_bcsr_set_closed(b.h, 2) == _capi.FE_EINVAL
