@@ -34,6 +34,10 @@ What it computes (Davydov & Kronbichler, arXiv:1907.01005):
   block pattern, computed here as an assembled SpMM.
 * Alg. 8 (Tmmult), by its definition C = A^T B: G_PY = P^T Y and G_PP = P^T P
   over the stored blocks, in FP64.
+* Alg. 7 (mmult) with a destination pattern, and the orbital-minimisation
+  quantities of Sec. 2: the energy (Eq. energy), its gradient (Eq. gradient,
+  built from Eqs. inner1/inner2 and G_ops1/G_ops2) and the directional
+  derivative tr(D^T G) (Eq. G_ops4).
 
 Every function is pinned by tests/test_oracle_pins.py against closed forms,
 brute force on tiny inputs, or numbers printed in the paper.
@@ -542,6 +546,44 @@ def apply_masked(H: sp.csr_matrix, Psp: sp.csc_matrix, blk: Blocking, pat: np.nd
 def gram(A: sp.spmatrix, B: sp.spmatrix) -> np.ndarray:
     """C = A^T B in FP64 (dense M x M)."""
     return np.asarray((A.T @ B).todense())
+
+
+def mmult_masked(A: sp.spmatrix, X: np.ndarray, blk: Blocking, pat: np.ndarray,
+                 cb_of_orb: np.ndarray) -> sp.csc_matrix:
+    """Alg. 7 with a destination pattern: C = mask(pattern) * (A X), A a sparse
+    (n_nodes, M) multivector, X a dense (M, M) matrix; the products that fall
+    outside the destination's block pattern are discarded (the truncation of
+    Alg. 7).  Returned as a sparse (n_nodes, M) matrix, FP64."""
+    AX = sp.coo_matrix(np.asarray(A @ X))
+    own = blk.owner_rank(AX.row)
+    keep = pat[own, cb_of_orb[AX.col]]
+    return sp.csc_matrix((AX.data[keep], (AX.row[keep], AX.col[keep])), shape=AX.shape)
+
+
+def om_energy(Psp: sp.spmatrix, H: sp.spmatrix, M: sp.spmatrix) -> float:
+    """Sec. 2, Eq. energy: E(Phi) = tr((2 I - Phi^T M Phi) Phi^T H Phi)."""
+    Hb = gram(Psp, H @ Psp)
+    Mb = gram(Psp, M @ Psp)
+    return float(np.trace((2.0 * np.eye(Hb.shape[0]) - Mb) @ Hb))
+
+
+def om_gradient(Psp: sp.spmatrix, PhiH: sp.spmatrix, PhiM: sp.spmatrix, blk: Blocking, pat: np.ndarray,
+                cb_of_orb: np.ndarray):
+    """Sec. 2, Eq. gradient with the operations of Eqs. inner1/inner2 and
+    G_ops1/G_ops2: Hbar = Phi^T Phi_H, Mbar = Phi^T Phi_M,
+    G = -2 Phi_M Hbar + 2 Phi_H (2 I - Mbar), truncated to the pattern.
+    Returns (G, Hbar, Mbar)."""
+    Hb = gram(Psp, PhiH)
+    Mb = gram(Psp, PhiM)
+    I = np.eye(Hb.shape[0])
+    G = mmult_masked(PhiM, -2.0 * Hb, blk, pat, cb_of_orb) + mmult_masked(PhiH, 2.0 * (2.0 * I - Mb), blk, pat,
+                                                                           cb_of_orb)
+    return sp.csc_matrix(G), Hb, Mb
+
+
+def trace_dot(D: sp.spmatrix, G: sp.spmatrix) -> float:
+    """Eq. G_ops4: tr(D^T G) = sum_alpha D_alpha . G_alpha."""
+    return float(D.multiply(G).sum())
 
 
 def apply_rows(mesh: BoxMesh, Vfunc, Psp: sp.csc_matrix, keys: np.ndarray) -> np.ndarray:

@@ -463,3 +463,51 @@ def test_apply_rows_matches_assembly():
     H = O.assemble(r.mesh, O.potential_fn(cfg))
     full = (H @ r.P).toarray()[keys]
     np.testing.assert_allclose(rows, full, rtol=0, atol=1e-13 * max(1.0, np.abs(full).max()))
+
+
+# ---------------------------------------------------------------------------
+# Post-multiplication (Alg. 7) and the orbital-minimisation gradient (Sec. 2)
+# ---------------------------------------------------------------------------
+def _tiny_state(name="tiny"):
+    cfg = inputs.get_config(name)
+    r = O.run(cfg, with_apply=False)
+    H = O.assemble(r.mesh, O.potential_fn(cfg))
+    M = O.assemble(r.mesh, None, mass=True)
+    return cfg, r, H, M
+
+
+def test_mmult_identity_and_brute_force():
+    """C = mask(A X): X = I gives A back (A lies in the pattern); a random X
+    matches an entry-by-entry sum over the stored entries of A."""
+    cfg, r, H, M = _tiny_state()
+    P = r.P.tocsc()
+    Mn = P.shape[1]
+    C = O.mmult_masked(P, np.eye(Mn), r.blk, r.pattern, r.cb_of_orb)
+    assert abs(C - P).max() == 0.0
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(Mn, Mn))
+    C = O.mmult_masked(P, X, r.blk, r.pattern, r.cb_of_orb).toarray()
+    Pd = P.toarray()
+    own = r.blk.owner_rank(np.arange(P.shape[0]))
+    for i in rng.choice(P.shape[0], 40, replace=False):
+        for b in range(Mn):
+            ref = sum(Pd[i, a] * X[a, b] for a in range(Mn) if Pd[i, a] != 0.0)
+            ref = ref if r.pattern[own[i], r.cb_of_orb[b]] else 0.0
+            assert abs(C[i, b] - ref) <= 1e-12 * (1 + abs(ref))
+
+
+def test_om_gradient_is_the_derivative_of_the_energy():
+    """tr(D^T G) equals the central finite difference of E(Phi + eps D) for a
+    random direction D inside the pattern (Sec. 2: the directional
+    derivative); the truncation of G to the pattern does not change it."""
+    cfg, r, H, M = _tiny_state()
+    P = r.P.tocsc()
+    G, Hb, Mb = O.om_gradient(P, (H @ P).tocsc(), (M @ P).tocsc(), r.blk, r.pattern, r.cb_of_orb)
+    rng = np.random.default_rng(5)
+    Dd = sp.csc_matrix((rng.normal(size=P.nnz), P.indices, P.indptr), shape=P.shape)   # same support as P
+    eps = 1e-5
+    fd = (O.om_energy(P + eps * Dd, H, M) - O.om_energy(P - eps * Dd, H, M)) / (2 * eps)
+    g = O.trace_dot(Dd, G)
+    assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (fd, g)
+    # the energy uses the same projections
+    assert O.om_energy(P, H, M) == pytest.approx(float(np.trace((2 * np.eye(Hb.shape[0]) - Mb) @ Hb)), rel=1e-14)
