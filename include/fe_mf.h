@@ -257,6 +257,30 @@ int fe_apply_H_gram_host(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_
                          double* G_PP_dev, const void* P_host, void* Y_host,
                          double* G_PY_host, double* G_PP_host, void* stream);
 
+/* Post-multiplication (Alg. 7, Sec. 3.6; Eqs. G_ops1/G_ops2):
+ *   C = alpha (A X + gamma A) + beta C, truncated to C's block pattern,
+ * where A and C have identical patterns and dtype (FE_EPATTERN otherwise) and
+ * X_dev is an M x M FP64 matrix in device memory, row-major, in the
+ * multivectors' column order.  The truncation of Alg. 7: products A_rk X_kj
+ * whose column block j is not stored in row block r are discarded.  FP32
+ * multivectors compute with X rounded to FP32 and FP32 FMAs (the result is
+ * FP32); FP64 ones in FP64.  C's row padding is written as zero.  C must
+ * be bound with a table buffer (its pattern tables are used); A needs values
+ * only.  C may not alias A (FE_EINVAL).  With gamma the orbital-minimisation gradient of Sec. 2,
+ * G = -2 Phi_M Hbar + 2 Phi_H (2 I - Mbar), is
+ *   fe_mmult(Phi_H, Mbar, -2, -2, 0, G);  fe_mmult(Phi_M, Hbar, -2, 0, 1, G).
+ * FE_EUNSUPPORTED if a row block's stored blocks hold more than 6144
+ * columns. */
+int fe_mmult(const fe_bcsr* A, const double* X_dev, double alpha, double gamma, double beta, fe_bcsr* C,
+             void* stream);
+
+/* Column-wise inner product tr(D^T G) = sum_alpha D_alpha . G_alpha over the
+ * stored entries (Eq. G_ops4), for the line search.  D and G have identical
+ * patterns and D is bound with a table buffer; the FP32 products are formed
+ * and summed in FP64.  *out_dev (one double in device memory) is
+ * overwritten. */
+int fe_trace_dot(const fe_bcsr* D, const fe_bcsr* G, double* out_dev, void* stream);
+
 /* ------------------------------------------------------------------------
  * Launch configuration, CUDA graph of the step, autotuner.  These shape how
  * the kernels of Alg. 6 / Alg. 8 are launched on this GPU; the paper's method

@@ -85,6 +85,8 @@ SIGNATURES = {
     "fe_gram_PtP": [_P, _P, _P],
     "fe_apply_H_gram": [_P, _P, _P, _P, _P, _P],
     "fe_apply_H_gram_host": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "fe_mmult": [_P, _P, _dbl, _dbl, _dbl, _P, _P],
+    "fe_trace_dot": [_P, _P, _P, _P],
     "fe_bcsr_set_launch": [_P, _i32, _i32, _i32],
     "fe_bcsr_get_launch": [_P, _pi32, _pi32, _pi32],
     "fe_bcsr_set_closed": [_P, _i32],

@@ -215,6 +215,22 @@ def gram_PtP(P: BCSR, G, stream=None):
     check(capi.fe_gram_PtP(P.h, _dptr(G), _stream(stream)))
 
 
+def mmult(A: BCSR, X, C: BCSR, alpha=1.0, gamma=0.0, beta=0.0, stream=None):
+    """C = alpha (A X + gamma A) + beta C on C's pattern (X: M x M FP64 on the device)."""
+    check(capi.fe_mmult(A.h, _dptr(X), float(alpha), float(gamma), float(beta), C.h, _stream(stream)))
+
+
+def trace_dot(D: BCSR, G: BCSR, out, stream=None):
+    """out[0] = tr(D^T G) (out: one FP64 on the device)."""
+    check(capi.fe_trace_dot(D.h, G.h, _dptr(out), _stream(stream)))
+
+
+def om_gradient(PhiH: BCSR, PhiM: BCSR, Hbar, Mbar, G: BCSR, stream=None):
+    """G = -2 Phi_M Hbar + 2 Phi_H (2 I - Mbar) on G's pattern (Sec. 2)."""
+    mmult(PhiH, Mbar, G, alpha=-2.0, gamma=-2.0, beta=0.0, stream=stream)
+    mmult(PhiM, Hbar, G, alpha=-2.0, gamma=0.0, beta=1.0, stream=stream)
+
+
 def apply_H_gram(mesh: Mesh, P: BCSR, Y: BCSR, G_PY, G_PP, stream=None):
     check(capi.fe_apply_H_gram(mesh.h, P.h, Y.h, _dptr(G_PY), _dptr(G_PP), _stream(stream)))
 

@@ -185,6 +185,50 @@ int apply_max_threads(int p);
 template <typename T>
 cudaError_t launch_gram(const GramArgs<T>& a, cudaStream_t s);
 
+// Post-multiplication C = alpha (A X + gamma A) + beta C (mmult.cu, Alg. 7)
+struct MmultItem {
+    int32_t r;          // row block
+    int32_t i0, j0;     // first row of the chunk, first union column of the output chunk
+    int32_t pad;
+};
+template <typename T>
+struct MmultArgs {
+    const T* A;
+    T* C;
+    const double* X;            // M x M, row-major, the multivectors' column order
+    int32_t n_cols;
+    int32_t wmax_union;         // largest union (columns of a row block's stored blocks)
+    const MmultItem* items;
+    int64_t n_items;
+    const int64_t* row_ptr;     // BCSR pattern on the device
+    const int32_t* col_idx;
+    const int64_t* blk_off;
+    const int32_t* cbp;
+    const int32_t* ld;
+    const int32_t* rb_rows;
+    double alpha, gamma, beta;
+    int32_t* status;
+};
+template <typename T>
+struct TraceArgs {
+    const T* D;
+    const T* G;
+    int64_t n_blocks;
+    const int32_t* block_rb;    // row block of each stored block
+    const int32_t* col_idx;
+    const int64_t* blk_off;
+    const int32_t* cbp;
+    const int32_t* ld;
+    const int32_t* rb_rows;
+    double* out;                // accumulated with atomics (zeroed by the caller)
+};
+template <typename T>
+size_t mmult_smem_bytes(int wmax_union);
+template <typename T>
+cudaError_t launch_mmult(const MmultArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_trace(const TraceArgs<T>& a, cudaStream_t s);
+
 cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s);
 constexpr int kProbeSinkSlots = 4096;   // per-CTA slots of the allocation-free probe (512 SMs x 8)
 // *too_many: 0 = ran; > 0 = the device needs that many slots (> kProbeSinkSlots);

@@ -188,6 +188,11 @@ struct fe_bcsr {
     std::vector<GramTcItem> tc_py, tc_pp;
     std::vector<int64_t> tc_uoff;
     std::vector<int32_t> tc_cinfo, tc_cglob, tc_rows;
+    // post-multiplication and trace (mmult.cu)
+    std::vector<MmultItem> mm_items;
+    std::vector<int32_t> block_rb, rb_rows;
+    int32_t wmax_union = 0;
+    size_t off_rowptr = 0, off_colidx = 0, off_blkoff = 0, off_blockrb = 0, off_rbrows = 0, off_mmitems = 0;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
     size_t off_tcg = 0, off_tcpy = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
     size_t off_units = 0, off_ld = 0, off_ticket = 0;
@@ -786,6 +791,21 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
             b->tc_rows.resize(R);
             for (int rr = 0; rr < R; ++rr) b->tc_rows[rr] = int32_t(m->rb_ptr[rr + 1] - m->rb_ptr[rr]);
         }
+        // ---- post-multiplication items: (row block, 64-row chunk, 64-column chunk)
+        b->rb_rows.resize(R);
+        b->block_rb.resize(nnz);
+        for (int rr = 0; rr < R; ++rr) {
+            const int rows = int(m->rb_ptr[rr + 1] - m->rb_ptr[rr]);
+            b->rb_rows[rr] = rows;
+            int W = 0;
+            for (int64_t k = row_ptr[rr]; k < row_ptr[rr + 1]; ++k) {
+                b->block_rb[k] = rr;
+                W += cbp[col_idx[k] + 1] - cbp[col_idx[k]];
+            }
+            b->wmax_union = std::max(b->wmax_union, W);
+            for (int i0 = 0; W > 0 && i0 < rows; i0 += 64)
+                for (int j0 = 0; j0 < W; j0 += 64) b->mm_items.push_back(MmultItem{rr, i0, j0, 0});
+        }
         size_t off = 0;
         b->off_tiles = off; off = align_up(off + b->tiles.size() * sizeof(Tile), 256);
         b->off_epy = off;   off = align_up(off + b->e_py.size() * sizeof(GramEntry), 256);
@@ -803,6 +823,12 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_tcrows = off; off = align_up(off + b->tc_rows.size() * sizeof(int32_t), 256);
         b->off_units = off; off = align_up(off + b->units.size() * sizeof(Unit), 256);
         b->off_ticket = off; off = align_up(off + 16, 256);   // work counter of the persistent launch
+        b->off_rowptr = off; off = align_up(off + (R + 1) * sizeof(int64_t), 256);
+        b->off_colidx = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int32_t), 256);
+        b->off_blkoff = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int64_t), 256);
+        b->off_blockrb = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int32_t), 256);
+        b->off_rbrows = off; off = align_up(off + R * sizeof(int32_t), 256);
+        b->off_mmitems = off; off = align_up(off + b->mm_items.size() * sizeof(MmultItem), 256);
         b->table_bytes = off;
     } catch (const std::bad_alloc&) {
         delete b;
@@ -875,6 +901,12 @@ int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
         FE_TRY_CUDA(put(b->off_tccg, b->tc_cglob.data(), b->tc_cglob.size() * sizeof(int32_t)), "fe_bcsr_bind: column ids");
         FE_TRY_CUDA(put(b->off_tcrows, b->tc_rows.data(), b->tc_rows.size() * sizeof(int32_t)), "fe_bcsr_bind: rows");
         FE_TRY_CUDA(put(b->off_units, b->units.data(), b->units.size() * sizeof(Unit)), "fe_bcsr_bind: units");
+        FE_TRY_CUDA(put(b->off_rowptr, b->row_ptr.data(), b->row_ptr.size() * sizeof(int64_t)), "fe_bcsr_bind: rows");
+        FE_TRY_CUDA(put(b->off_colidx, b->col_idx.data(), b->col_idx.size() * sizeof(int32_t)), "fe_bcsr_bind: columns");
+        FE_TRY_CUDA(put(b->off_blkoff, b->blk_off.data(), b->blk_off.size() * sizeof(int64_t)), "fe_bcsr_bind: offsets");
+        FE_TRY_CUDA(put(b->off_blockrb, b->block_rb.data(), b->block_rb.size() * sizeof(int32_t)), "fe_bcsr_bind: blocks");
+        FE_TRY_CUDA(put(b->off_rbrows, b->rb_rows.data(), b->rb_rows.size() * sizeof(int32_t)), "fe_bcsr_bind: rows");
+        FE_TRY_CUDA(put(b->off_mmitems, b->mm_items.data(), b->mm_items.size() * sizeof(MmultItem)), "fe_bcsr_bind: mmult items");
         // the source arrays are members of the handle; make sure the copies
         // are done before a later re-bind could free them
         FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_bcsr_bind: synchronize");
@@ -1132,6 +1164,78 @@ int fe_bcsr_set_launch(fe_bcsr* b, int32_t persistent, int32_t ctas_per_sm, int3
     b->ctas_per_sm = ctas_per_sm;
     b->cells_per_round = cells_per_round;
     return FE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+int mmult_impl(const fe_bcsr* A, const double* X, double alpha, double gamma, double beta, fe_bcsr* C,
+               cudaStream_t s) {
+    MmultArgs<T> a;
+    const char* t = static_cast<const char*>(C->tables);     // the pattern tables (A's are identical)
+    a.A = static_cast<const T*>(A->values);
+    a.C = static_cast<T*>(C->values);
+    a.X = X;
+    a.n_cols = A->n_cols;
+    a.wmax_union = std::max(1, C->wmax_union);
+    a.items = reinterpret_cast<const MmultItem*>(t + C->off_mmitems);
+    a.n_items = (int64_t)C->mm_items.size();
+    a.row_ptr = reinterpret_cast<const int64_t*>(t + C->off_rowptr);
+    a.col_idx = reinterpret_cast<const int32_t*>(t + C->off_colidx);
+    a.blk_off = reinterpret_cast<const int64_t*>(t + C->off_blkoff);
+    a.cbp = reinterpret_cast<const int32_t*>(t + C->off_cbp);
+    a.ld = reinterpret_cast<const int32_t*>(t + C->off_ld);
+    a.rb_rows = reinterpret_cast<const int32_t*>(t + C->off_rbrows);
+    a.alpha = alpha;
+    a.gamma = gamma;
+    a.beta = beta;
+    a.status = A->mesh ? A->mesh->status : nullptr;
+    FE_TRY_CUDA(launch_mmult<T>(a, s), "fe_mmult: kernel launch");
+    return FE_OK;
+}
+
+template <typename T>
+int trace_impl(const fe_bcsr* D, const fe_bcsr* G, double* out, cudaStream_t s) {
+    TraceArgs<T> a;
+    const char* t = static_cast<const char*>(D->tables);
+    a.D = static_cast<const T*>(D->values);
+    a.G = static_cast<const T*>(G->values);
+    a.n_blocks = (int64_t)D->col_idx.size();
+    a.block_rb = reinterpret_cast<const int32_t*>(t + D->off_blockrb);
+    a.col_idx = reinterpret_cast<const int32_t*>(t + D->off_colidx);
+    a.blk_off = reinterpret_cast<const int64_t*>(t + D->off_blkoff);
+    a.cbp = reinterpret_cast<const int32_t*>(t + D->off_cbp);
+    a.ld = reinterpret_cast<const int32_t*>(t + D->off_ld);
+    a.rb_rows = reinterpret_cast<const int32_t*>(t + D->off_rbrows);
+    a.out = out;
+    FE_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s), "fe_trace_dot: zero");
+    FE_TRY_CUDA(launch_trace<T>(a, s), "fe_trace_dot: kernel launch");
+    return FE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_mmult(const fe_bcsr* A, const double* X, double alpha, double gamma, double beta, fe_bcsr* C, void* stream) {
+    int rc = check_pair("fe_mmult", nullptr, C, A);   // C carries the tables, A the values
+    if (rc) return rc;
+    if (!X && A->n_values > 0) return fail(FE_EINVAL, "fe_mmult: X is NULL");
+    if (A == C) return fail(FE_EINVAL, "fe_mmult: C may not alias A");
+    if ((size_t)C->wmax_union * 16 > 96 * 1024) return fail(FE_EUNSUPPORTED, "fe_mmult: a row block holds %d columns", C->wmax_union);
+    cudaStream_t s = (cudaStream_t)stream;
+    return A->dtype == FE_F64 ? mmult_impl<double>(A, X, alpha, gamma, beta, C, s)
+                              : mmult_impl<float>(A, X, alpha, gamma, beta, C, s);
+}
+
+int fe_trace_dot(const fe_bcsr* D, const fe_bcsr* G, double* out, void* stream) {
+    int rc = check_pair("fe_trace_dot", nullptr, D, G);
+    if (rc) return rc;
+    if (!out) return fail(FE_EINVAL, "fe_trace_dot: out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    return D->dtype == FE_F64 ? trace_impl<double>(D, G, out, s) : trace_impl<float>(D, G, out, s);
 }
 
 int fe_bcsr_set_closed(fe_bcsr* b, int32_t closed) {
