@@ -315,6 +315,44 @@ def time_graph(pb, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def time_om(pb, steps):
+    """The rest of an orbital-minimisation gradient evaluation on the step's
+    workload (Sec. 2): Phi_M = M P, Mbar = P^T Phi_M, the two post-
+    multiplications of the gradient and tr(D^T G); CUDA-event medians (ms)."""
+    import torch
+    from paper_1907_01005_gb300 import BCSR, apply_M, gram_PtY, mmult, trace_dot
+    d = pb.dev
+    M = pb.n_cols
+
+    def like():
+        B = BCSR(pb.mesh, pb.cbp, pb.row_ptr, pb.col_idx, pb.dtype)
+        v, t = B.alloc()
+        B.bind(v, t)
+        return B
+    YM, G, D = like(), like(), like()
+    D.values.normal_()
+    Mb = torch.zeros((M, M), dtype=torch.float64, device="cuda")
+    g = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    names = ("apply_M", "gram_M", "mmult_1", "mmult_2", "trace")
+    calls = (lambda: apply_M(pb.mesh, pb.P, YM, s), lambda: gram_PtY(pb.P, YM, Mb, s),
+             lambda: mmult(pb.Y, Mb, G, -2.0, -2.0, 0.0, s), lambda: mmult(YM, d["G_PY"], G, -2.0, 0.0, 1.0, s),
+             lambda: trace_dot(D, G, g, s))
+    for _ in range(3):
+        for f in calls:
+            f()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(steps)]
+    for k in range(steps):
+        ev[k][0].record(s)
+        for i, f in enumerate(calls):
+            f()
+            ev[k][i + 1].record(s)
+    torch.cuda.synchronize()
+    out = {n: statistics.median(e[i].elapsed_time(e[i + 1]) for e in ev) for i, n in enumerate(names)}
+    out["total_ms"] = sum(out.values())
+    return out
+
+
 def serving_run(args, dtype=1):
     """Poisson stream of apply_H + Gram requests through the continuous-batching
     server: a pool of distinct workloads drawn from the serving mix, arrivals
@@ -475,6 +513,15 @@ def main():
             "alu_peaks_tflops": {"fp32": probe_alu(1) / 1e12, "fp32x2": probe_alu(3) / 1e12,
                                  "fp64": fp64_peak / 1e12},
             "gpu_launches": 3 * args.steps, "clocks": clk}
+
+    # the rest of an orbital-minimisation gradient evaluation (NEXT rows f1, f3)
+    om = time_om(pb, max(10, args.steps // 10))
+    t_mm = om["mmult_1"] * 1e-3
+    om["mmult_roofline"] = {"bound": "alu", "achieved": info.gram_flops / t_mm / 1e12, "peak": fp32_peak / 1e12,
+                            "unit": "TFLOP/s", "frac": info.gram_flops / t_mm / fp32_peak,
+                            "hbm_frac": 2 * nnz * s / t_mm / 1e9 / hbm_peak}
+    om["gradient_ms"] = ms_step + om["total_ms"]      # H P, Hbar, P^T P (the step) plus the above
+    line["om"] = om
 
     # FP64 path on the same workload
     if not args.no_fp64:

@@ -206,6 +206,8 @@ struct MmultArgs {
     const int32_t* cbp;
     const int32_t* ld;
     const int32_t* rb_rows;
+    const int32_t* ucol0;       // first union column of each stored block within its row block
+    const int32_t* rb_union;    // union columns of each row block
     double alpha, gamma, beta;
     int32_t* status;
 };

@@ -190,9 +190,10 @@ struct fe_bcsr {
     std::vector<int32_t> tc_cinfo, tc_cglob, tc_rows;
     // post-multiplication and trace (mmult.cu)
     std::vector<MmultItem> mm_items;
-    std::vector<int32_t> block_rb, rb_rows;
+    std::vector<int32_t> block_rb, rb_rows, ucol0, rb_union;
     int32_t wmax_union = 0;
     size_t off_rowptr = 0, off_colidx = 0, off_blkoff = 0, off_blockrb = 0, off_rbrows = 0, off_mmitems = 0;
+    size_t off_ucol0 = 0, off_rbunion = 0;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
     size_t off_tcg = 0, off_tcpy = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
     size_t off_units = 0, off_ld = 0, off_ticket = 0;
@@ -793,15 +794,19 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         }
         // ---- post-multiplication items: (row block, 64-row chunk, 64-column chunk)
         b->rb_rows.resize(R);
+        b->rb_union.resize(R);
         b->block_rb.resize(nnz);
+        b->ucol0.resize(nnz);
         for (int rr = 0; rr < R; ++rr) {
             const int rows = int(m->rb_ptr[rr + 1] - m->rb_ptr[rr]);
             b->rb_rows[rr] = rows;
             int W = 0;
             for (int64_t k = row_ptr[rr]; k < row_ptr[rr + 1]; ++k) {
                 b->block_rb[k] = rr;
+                b->ucol0[k] = W;
                 W += cbp[col_idx[k] + 1] - cbp[col_idx[k]];
             }
+            b->rb_union[rr] = W;
             b->wmax_union = std::max(b->wmax_union, W);
             for (int i0 = 0; W > 0 && i0 < rows; i0 += 64)
                 for (int j0 = 0; j0 < W; j0 += 64) b->mm_items.push_back(MmultItem{rr, i0, j0, 0});
@@ -829,6 +834,8 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_blockrb = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int32_t), 256);
         b->off_rbrows = off; off = align_up(off + R * sizeof(int32_t), 256);
         b->off_mmitems = off; off = align_up(off + b->mm_items.size() * sizeof(MmultItem), 256);
+        b->off_ucol0 = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int32_t), 256);
+        b->off_rbunion = off; off = align_up(off + R * sizeof(int32_t), 256);
         b->table_bytes = off;
     } catch (const std::bad_alloc&) {
         delete b;
@@ -907,6 +914,8 @@ int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
         FE_TRY_CUDA(put(b->off_blockrb, b->block_rb.data(), b->block_rb.size() * sizeof(int32_t)), "fe_bcsr_bind: blocks");
         FE_TRY_CUDA(put(b->off_rbrows, b->rb_rows.data(), b->rb_rows.size() * sizeof(int32_t)), "fe_bcsr_bind: rows");
         FE_TRY_CUDA(put(b->off_mmitems, b->mm_items.data(), b->mm_items.size() * sizeof(MmultItem)), "fe_bcsr_bind: mmult items");
+        FE_TRY_CUDA(put(b->off_ucol0, b->ucol0.data(), b->ucol0.size() * sizeof(int32_t)), "fe_bcsr_bind: union");
+        FE_TRY_CUDA(put(b->off_rbunion, b->rb_union.data(), b->rb_union.size() * sizeof(int32_t)), "fe_bcsr_bind: union");
         // the source arrays are members of the handle; make sure the copies
         // are done before a later re-bind could free them
         FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_bcsr_bind: synchronize");
@@ -1188,6 +1197,8 @@ int mmult_impl(const fe_bcsr* A, const double* X, double alpha, double gamma, do
     a.cbp = reinterpret_cast<const int32_t*>(t + C->off_cbp);
     a.ld = reinterpret_cast<const int32_t*>(t + C->off_ld);
     a.rb_rows = reinterpret_cast<const int32_t*>(t + C->off_rbrows);
+    a.ucol0 = reinterpret_cast<const int32_t*>(t + C->off_ucol0);
+    a.rb_union = reinterpret_cast<const int32_t*>(t + C->off_rbunion);
     a.alpha = alpha;
     a.gamma = gamma;
     a.beta = beta;

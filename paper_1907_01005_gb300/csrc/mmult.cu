@@ -11,6 +11,9 @@
 // Work item: (row block, 64-row chunk, 64-column chunk of the union).  256
 // threads, each owning a 4 x 4 micro-tile; the union is walked in k-tiles of
 // 32 columns staged in shared memory (X rounded to the working precision).
+#include <algorithm>
+#include <type_traits>
+
 #include "fe_internal.h"
 
 namespace femf {
@@ -28,41 +31,33 @@ __global__ void __launch_bounds__(256) mmult_kernel(const MmultArgs<T> a) {
     int* sUcol = sUld + a.wmax_union;                           // [wmax] global column
     __shared__ T sA[kMT][kKT + 1];
     __shared__ T sX[kKT][kNT + 1];
-    __shared__ int sW, sRows;
 
     const MmultItem it = a.items[blockIdx.x];
     const int tid = threadIdx.x;
     const int r = it.r;
     const int64_t b0 = a.row_ptr[r], b1 = a.row_ptr[r + 1];
-    if (tid == 0) {
-        int W = 0;
-        for (int64_t k = b0; k < b1; ++k) {
-            const int c = a.col_idx[k];
-            W += a.cbp[c + 1] - a.cbp[c];
-        }
-        sW = W;
-        sRows = a.rb_rows[r];
-    }
-    __syncthreads();
-    const int W = sW, rows = sRows;
+    const int W = a.rb_union[r], rows = a.rb_rows[r];
     // work-list check: the union fits the tables the launch sized
-    if (W > a.wmax_union || it.i0 >= rows || it.j0 >= W) {
+    if (W > a.wmax_union || W < 1 || it.i0 >= rows || it.j0 >= W) {
         if (tid == 0 && a.status) atomicExch(a.status, kDevBadTile);
         return;
     }
-    if (tid == 0) {
-        int u = 0;
-        for (int64_t k = b0; k < b1; ++k) {
-            const int c = a.col_idx[k], w = a.cbp[c + 1] - a.cbp[c], ld = a.ld[c];
-            for (int q = 0; q < w; ++q, ++u) {
-                sUoff[u] = a.blk_off[k] + q;
-                sUld[u] = ld;
-                sUcol[u] = a.cbp[c] + q;
-            }
+    // union-column map, one thread per stored block of the row block
+    for (int64_t k = b0 + tid; k < b1; k += blockDim.x) {
+        const int c = a.col_idx[k], w = a.cbp[c + 1] - a.cbp[c], ld = a.ld[c], u0 = a.ucol0[k];
+        if (u0 < 0 || u0 + w > W) {
+            if (a.status) atomicExch(a.status, kDevBadTile);
+            continue;
+        }
+        for (int q = 0; q < w; ++q) {
+            sUoff[u0 + q] = a.blk_off[k] + q;
+            sUld[u0 + q] = ld;
+            sUcol[u0 + q] = a.cbp[c] + q;
         }
     }
     __syncthreads();
 
+    const T alpha = T(a.alpha), gamma = T(a.gamma), beta = T(a.beta);
     const int ty = tid >> 4, tx = tid & 15;       // rows ty*4 .., columns tx*4 ..
     T acc[4][4];
 #pragma unroll
@@ -111,11 +106,12 @@ __global__ void __launch_bounds__(256) mmult_kernel(const MmultArgs<T> a) {
             const int u = it.j0 + tx * 4 + j;
             if (u >= W) continue;
             const int64_t o = sUoff[u] + (int64_t)row * sUld[u];
-            double v = (double)acc[i][j];
-            if (a.gamma != 0.0) v += a.gamma * (double)a.A[o];
-            v *= a.alpha;
-            if (a.beta != 0.0) v += a.beta * (double)a.C[o];
-            a.C[o] = T(v);
+            // in the working precision (FP64 arithmetic runs at 1/64 rate here)
+            T v = acc[i][j];
+            if (gamma != T(0)) v = fma(gamma, a.A[o], v);
+            v *= alpha;
+            if (beta != T(0)) v = fma(beta, a.C[o], v);
+            a.C[o] = v;
         }
     }
     // padding columns of the row chunk's blocks are written as zero (once)
@@ -132,25 +128,58 @@ __global__ void __launch_bounds__(256) mmult_kernel(const MmultArgs<T> a) {
     }
 }
 
-// tr(D^T G): one warp per stored block, FP64 products of the stored entries
-// (FP32 x FP32 products are exact in FP64), warp sum, one atomic per block.
+// Exact product a b = p + e (e = fma(a, b, -p)) added into the running sum
+// (s, comp) with a compensated (two-sum) step: the per-lane block sum keeps
+// about twice the working precision, without FP64 arithmetic per entry.
+template <typename T>
+__device__ __forceinline__ void add_product(T a, T b, T& s, T& comp) {
+    const T p = a * b, e = fma(a, b, -p);
+    const T t = s + p, bp = t - s;
+    comp += (s - (t - bp)) + (p - bp) + e;
+    s = t;
+}
+
+// tr(D^T G): warps take stored blocks in turn; lanes walk a block's 16-byte
+// chunks (the chunk index within a row advances by 32 mod chunks-per-row, no
+// division), padding columns masked.  Per lane the block's products are
+// summed with the compensated step above and added to an FP64 lane total;
+// lane totals are reduced in the warp and the CTA, one atomic per CTA.
 template <typename T>
 __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs<T> a) {
-    const int64_t k = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (k >= a.n_blocks) return;
-    const int lane = threadIdx.x & 31;
-    const int r = a.block_rb[k];
-    const int c = a.col_idx[k], w = a.cbp[c + 1] - a.cbp[c], ld = a.ld[c];
-    const int rows = a.rb_rows[r];
-    const int64_t o = a.blk_off[k];
-    double s = 0.0;
-    for (int e = lane; e < rows * w; e += 32) {
-        const int64_t idx = o + (int64_t)(e / w) * ld + e % w;
-        s = fma((double)a.D[idx], (double)a.G[idx], s);
+    constexpr int CH = 16 / sizeof(T);
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    __shared__ double sRed[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double total = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * 8 + wid; k < a.n_blocks; k += (int64_t)gridDim.x * 8) {
+        const int r = a.block_rb[k];
+        const int c = a.col_idx[k], w = a.cbp[c + 1] - a.cbp[c], ld = a.ld[c];
+        const int nq = ld / CH, n = a.rb_rows[r] * nq, step = 32 % nq;
+        const V* Dv = reinterpret_cast<const V*>(a.D + a.blk_off[k]);
+        const V* Gv = reinterpret_cast<const V*>(a.G + a.blk_off[k]);
+        T s = T(0), comp = T(0);
+        int q = lane % nq;
+        for (int e = lane; e < n; e += 32) {
+            const V dv = Dv[e], gv = Gv[e];
+            const T* dp = reinterpret_cast<const T*>(&dv);
+            const T* gp = reinterpret_cast<const T*>(&gv);
+#pragma unroll
+            for (int h = 0; h < CH; ++h)
+                if (q * CH + h < w) add_product(dp[h], gp[h], s, comp);
+            q += step;
+            if (q >= nq) q -= nq;
+        }
+        total += (double)s + (double)comp;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0 && s != 0.0) atomicAdd(a.out, s);
+    for (int off = 16; off > 0; off >>= 1) total += __shfl_xor_sync(0xffffffffu, total, off);
+    if (lane == 0) sRed[wid] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i) t += sRed[i];
+        if (t != 0.0) atomicAdd(a.out, t);
+    }
 }
 
 }  // namespace
@@ -177,7 +206,11 @@ cudaError_t launch_mmult(const MmultArgs<T>& a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_trace(const TraceArgs<T>& a, cudaStream_t s) {
     if (a.n_blocks == 0) return cudaSuccess;
-    trace_kernel<T><<<(unsigned)((a.n_blocks + 7) / 8), 256, 0, s>>>(a);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (a.n_blocks + 7) / 8;
+    trace_kernel<T><<<(unsigned)std::min<int64_t>(need, 8 * (int64_t)sms), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
