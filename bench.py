@@ -315,6 +315,32 @@ def time_graph(pb, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def time_cellmat(pb, steps):
+    """Medians (ms) of fe_apply_H and fe_apply_M in the cell-matrix form (FP32,
+    p <= 2, element matrices on the tensor cores), the form restored after."""
+    import torch
+    from paper_1907_01005_gb300 import FORM_CELLMAT, FORM_SUMFAC, apply_H, apply_M
+    s = torch.cuda.current_stream()
+    pb.P.set_form(FORM_CELLMAT)
+    out = {}
+    try:
+        for name, f in (("apply_H", apply_H), ("apply_M", apply_M)):
+            for _ in range(3):
+                f(pb.mesh, pb.P, pb.Y, s)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+            ev[0].record(s)
+            for k in range(steps):
+                f(pb.mesh, pb.P, pb.Y, s)
+                ev[k + 1].record(s)
+            torch.cuda.synchronize()
+            out[name] = statistics.median(ev[k].elapsed_time(ev[k + 1]) for k in range(steps))
+        if pb.mesh.check_device() != 0:
+            raise RuntimeError("device status word set by the cell-matrix kernel")
+    finally:
+        pb.P.set_form(FORM_SUMFAC)
+    return out
+
+
 def time_om(pb, steps):
     """The rest of an orbital-minimisation gradient evaluation on the step's
     workload (Sec. 2): Phi_M = M P, Mbar = P^T Phi_M, the two post-
@@ -522,6 +548,26 @@ def main():
                             "hbm_frac": 2 * nnz * s / t_mm / 1e9 / hbm_peak}
     om["gradient_ms"] = ms_step + om["total_ms"]      # H P, Hbar, P^T P (the step) plus the above
     line["om"] = om
+
+    # cell-matrix form of the apply (NEXT row f2): element matrices as dense
+    # TF32 tensor-core products with a 3-term split; work per active
+    # cell-column: 3 splits x 2 (n^3)^2 flops for each of K_L, S3, Sb3 (H) or
+    # M_c (M)
+    if cfg.p <= 2:
+        cm = time_cellmat(pb, max(10, args.steps // 4))
+        n3 = (cfg.p + 1) ** 3
+        tf32_peak = bf16_peak * 1.1 / 2.25         # measured bf16 x nominal TF32/bf16 ratio
+        wH = info.active_cell_cols * 3 * 3 * 2 * n3 * n3
+        wM = info.active_cell_cols * 3 * 2 * n3 * n3
+        tH = cm["apply_H"] * 1e-3
+        line["cellmat"] = {
+            "apply_H_ms": cm["apply_H"], "apply_M_ms": cm["apply_M"],
+            "vs_sumfac_apply": cm["apply_H"] / (1e3 * t_apply),
+            "tf32_tflops_H": wH / tH / 1e12, "tf32_tflops_M": wM / (cm["apply_M"] * 1e-3) / 1e12,
+            "roofline": {"bound": "tensor", "achieved": wH / tH / 1e12, "peak": tf32_peak / 1e12,
+                         "unit": "TFLOP/s", "frac": wH / tH / tf32_peak,
+                         "peak_source": "measured bf16_tflops x 1.1/2.25 (nominal TF32/bf16)",
+                         "hbm_frac": apply_bytes / tH / 1e9 / hbm_peak}}
 
     # FP64 path on the same workload
     if not args.no_fp64:

@@ -60,6 +60,10 @@ extern "C" {
 #define FE_F32 1            /* FP32 storage, FP32 cell arithmetic, FP64 Gram accumulation */
 #define FE_F64 2            /* FP64 storage and arithmetic throughout */
 
+/* Forms of the cell operator (fe_bcsr_set_form) */
+#define FE_FORM_SUMFAC 0    /* sum factorisation on the FP32/FP64 ALUs (Sec. 3.5, Alg. 6) */
+#define FE_FORM_CELLMAT 1   /* element matrices as dense products on the tensor cores (Sec. 3.2) */
+
 typedef struct fe_mesh fe_mesh;
 typedef struct fe_bcsr fe_bcsr;
 
@@ -112,7 +116,8 @@ int fe_mesh_node_coords(const fe_mesh* mesh, double* xyz);
  * [row block r][cell c = cx + 2 cy + 4 cz of the patch][qz][qy][qx]. */
 int fe_mesh_quad_points(const fe_mesh* mesh, double* xyz);
 
-/* Bytes of device workspace the mesh needs (tables and the device status word). */
+/* Bytes of device workspace the mesh needs: the device status word and, for
+ * p <= 2, the constant operands of the cell-matrix form (48 KB at p = 2). */
 int fe_mesh_workspace_bytes(const fe_mesh* mesh, size_t* bytes);
 
 /* Copies the mesh tables into the caller's device buffer `workspace_dev`
@@ -312,6 +317,27 @@ int fe_bcsr_get_launch(const fe_bcsr* P, int32_t* persistent, int32_t* ctas_per_
  * flag other than 0 or 1. */
 int fe_bcsr_set_closed(fe_bcsr* P, int32_t closed);
 int fe_bcsr_get_closed(const fe_bcsr* P, int32_t* closed);
+
+/* Form of the cell operator that fe_apply_H and fe_apply_M use for source P.
+ *   FE_FORM_SUMFAC  (default) sum factorisation, Alg. 6, on the FP32 or FP64
+ *                   ALUs (every degree and dtype).
+ *   FE_FORM_CELLMAT the element view H = sum_K P_K^T H_K P_K (Sec. 3.2, Eq.
+ *                   fe_matrices_cell_based) with the element matrices applied
+ *                   as dense products per cell, the approach the paper
+ *                   compares against as "FE op. (BCSR gemm)" (Sec. 4.2).  On
+ *                   the box mesh all cells share K_L (kinetic), S3 and Sb3, so
+ *                   H_K u = K_L u + Sb3 (|J| V_K o S3 u) runs as two rounds of
+ *                   TF32 tensor-core products with a 3-term split (FP32
+ *                   accuracy); M_K u = (|J| Sb3 S3) u as one.  FE_F32 and
+ *                   p <= 2 only.  Its launch is persistent (2 CTAs per SM) and
+ *                   uses the work counter in P's tables, like the persistent
+ *                   sum-factorised launch: two calls with the same P must not
+ *                   run concurrently.
+ * The result equals the other form's up to FP32 rounding (both within the
+ * 1e-5 tolerance of the FP64 operator).  FE_EINVAL for another value,
+ * FE_EUNSUPPORTED for FE_FORM_CELLMAT with FE_F64 values or p > 2. */
+int fe_bcsr_set_form(fe_bcsr* P, int32_t form);
+int fe_bcsr_get_form(const fe_bcsr* P, int32_t* form);
 
 /* CUDA graph of one fe_apply_H_gram step with the given (already bound)
  * buffers: runs the step once eagerly on `stream` (this sets kernel

@@ -21,6 +21,8 @@ FE_ESTATE = -6
 FE_EUNSUPPORTED = -7
 FE_F32 = 1
 FE_F64 = 2
+FORM_SUMFAC = 0      # FE_FORM_SUMFAC
+FORM_CELLMAT = 1     # FE_FORM_CELLMAT
 
 _NAMES = {FE_EINVAL: "FE_EINVAL", FE_ENOMEM: "FE_ENOMEM", FE_EPATTERN: "FE_EPATTERN",
           FE_ECUDA: "FE_ECUDA", FE_EDEVICE: "FE_EDEVICE", FE_ESTATE: "FE_ESTATE",
@@ -91,6 +93,8 @@ SIGNATURES = {
     "fe_bcsr_get_launch": [_P, _pi32, _pi32, _pi32],
     "fe_bcsr_set_closed": [_P, _i32],
     "fe_bcsr_get_closed": [_P, _pi32],
+    "fe_bcsr_set_form": [_P, _i32],
+    "fe_bcsr_get_form": [_P, _pi32],
     "fe_graph_create": [_P, _P, _P, _P, _P, _P, C.POINTER(_P)],
     "fe_graph_launch": [_P, _P],
     "fe_graph_destroy": [_P],

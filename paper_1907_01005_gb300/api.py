@@ -8,7 +8,7 @@ import ctypes as C
 import numpy as np
 
 from . import _capi as capi
-from ._capi import FE_F32, FE_F64, check
+from ._capi import FE_F32, FE_F64, FORM_CELLMAT, FORM_SUMFAC, check
 
 
 def _hptr(a: np.ndarray) -> C.c_void_p:
@@ -191,6 +191,17 @@ class BCSR:
         v = C.c_int32()
         check(capi.fe_bcsr_get_closed(self.h, C.byref(v)))
         return bool(v.value)
+
+    def set_form(self, form: int):
+        """Form of the cell operator of fe_apply_H / fe_apply_M with this P as
+        source: FORM_SUMFAC (sum factorisation) or FORM_CELLMAT (element
+        matrices on the tensor cores; FP32, p <= 2)."""
+        check(capi.fe_bcsr_set_form(self.h, int(form)))
+
+    def get_form(self) -> int:
+        v = C.c_int32()
+        check(capi.fe_bcsr_get_form(self.h, C.byref(v)))
+        return v.value
 
     def get_launch(self):
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()

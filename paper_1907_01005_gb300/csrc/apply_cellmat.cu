@@ -1,0 +1,496 @@
+// Cell-matrix form of the apply for p <= 2, FP32, on the tcgen05 tensor cores.
+//
+// The element view of the operator (Sec. 3.2, Eq. fe_matrices_cell_based):
+// H = sum_K P_K^T H_K P_K, with the element matrices applied as dense
+// products on the element level (the "FE op. (BCSR gemm)" flavour of Sec. 4.2).
+// On the box meshes here every cell has the same affine geometry, so
+//   H_K u = K_L u + Sb3 (|J| V_K o (S3 u)),
+// with three matrices shared by all cells: K_L = Sb3 L_c S3 (kinetic part,
+// L_c the collocation Laplacian at the Gauss points), S3 = S x S x S
+// (interpolation to the Gauss points) and Sb3 (its weighted transpose); only
+// the potential V_K at the cell's Gauss points differs between cells.  The
+// mass operator is M_K u = (|J| Sb3 S3) u.
+//
+// Work decomposition: the packed work units of the register kernel (a patch
+// and up to 32 columns of its column blocks).  Thread (cell, lane) owns row
+// m = 32 cell + lane of the operand A[m][k] = u of its cell-column at cell
+// node k, so the unit is two 128-row tiles.  Per tile:
+//   stage 1  D[:, 0:npad]      = A K_L^T,  D[:, npad:2 npad] = A S3^T   (N = 2 npad)
+//   stage 2  D[:, 0:npad]     += (|J| V o D[:, npad:2 npad]) Sb3^T     (N = npad)
+// as tcgen05.mma kind::tf32 with the accumulators in tensor memory.  FP32
+// accuracy comes from a 3-term TF32 split of both operands,
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi   (a_hi = TF32 rounding of a),
+// which leaves an error of about 2^-21 relative per product.
+//
+// Data movement is that of the register kernel: 16-byte cp.async gather of the
+// patch tensor, shared-memory atomics of the cells' results into a zeroed
+// patch tensor (here it reuses the gather buffer), 16-byte vector reductions
+// into Y.  The constant operand tiles (both parts of K_L, S3, Sb3) are copied
+// once per CTA; CTAs are persistent and take units from a work counter.
+#include <algorithm>
+#include <cstdint>
+
+#include "fe_internal.h"
+#include "unit_common.cuh"
+
+namespace femf {
+namespace {
+
+template <int P>
+struct CmGeo {
+    static constexpr int N = P + 1, NP = 2 * P + 1, NPN = NP * NP * NP, N3 = N * N * N;
+    static constexpr int NPAD = cellmat_npad(P);   // cell nodes padded: MMA N of one matrix
+    static constexpr int KSTEPS = (N3 + 7) / 8;    // K = 8 per TF32 MMA
+    static constexpr int L = kUnitLanes;
+    static constexpr int THREADS = 8 * L;          // one A row per thread: 2 tiles of 128
+    static constexpr int CH = 4;                   // floats per 16-byte chunk
+    static constexpr int MAXCH = kUnitLdSum / CH;
+    static constexpr int TEN = NPN * kUnitLdSum;   // floats of the patch tensor
+    static constexpr int TILE = 128 * 128;         // bytes of a 128-row operand tile (rows of 32 floats)
+    // dynamic shared memory, from a 1024-byte aligned base (the period of the
+    // 128-byte swizzle): A high parts (2 tiles), A low parts, the constant
+    // set (B1 high/low: 2 npad rows each; B2 high/low: npad rows each), the
+    // patch tensor, V at the Gauss points of the 8 cells
+    static constexpr int OFF_AH = 0;
+    static constexpr int OFF_AL = 2 * TILE;
+    static constexpr int OFF_B1H = 4 * TILE;
+    static constexpr int OFF_B1L = OFF_B1H + 2 * NPAD * 128;
+    static constexpr int OFF_B2H = OFF_B1L + 2 * NPAD * 128;
+    static constexpr int OFF_B2L = OFF_B2H + NPAD * 128;
+    static constexpr int OFF_U = OFF_B2L + NPAD * 128;
+    static constexpr int OFF_V = OFF_U + TEN * 4;
+    static constexpr int bytes = OFF_V + 8 * N3 * 4 + 1024;   // + alignment slack
+    static constexpr int TMEM_COLS = 4 * NPAD;                 // 2 tiles x 2 npad FP32 columns
+    static constexpr int SET_FLOATS = cellmat_set_floats(P);
+    static_assert(OFF_B1H % 1024 == 0 && OFF_B1L % 1024 == 0 && OFF_B2H % 1024 == 0 && OFF_B2L % 1024 == 0,
+                  "operand tiles must start on the swizzle period");
+    static_assert((OFF_B2L + NPAD * 128 - OFF_B1H) == cellmat_set_floats(P) * 4, "constant set size");
+    static_assert(OFF_U % 16 == 0 && OFF_V % 16 == 0, "16-byte copies");
+    static_assert(TMEM_COLS == 64 || TMEM_COLS == 128, "tensor-memory allocation: power of two >= 32");
+};
+
+// ---- PTX wrappers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major operand, rows of 128 bytes with the
+// 128-byte swizzle, 8-row groups 1024 bytes apart (stride byte offset); the
+// leading byte offset is unused for this layout (one swizzle atom along K).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (16 B, unused)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                 // layout: 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major.
+__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits until the barrier's phase `parity` has completed, for at most
+// `limit_ns`; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// 32 lanes x NC consecutive FP32 columns of tensor memory: thread i of the
+// warp receives lane (32 (warp % 4) + i), columns col .. col + NC - 1.  The
+// wait is tied to the destination registers so no use moves above it.
+template <int NC>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[NC]);
+template <>
+__device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <>
+__device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])::"memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// TF32 rounding (to nearest, ties away) of x: the high part of the split.
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Row r of a 128-row tile pair (high parts at hi, low parts at lo): values
+// x[0 .. 4 nch - 1] as 16-byte chunks, chunk c stored at chunk c ^ (r & 7).
+template <int NCH>
+__device__ __forceinline__ void store_row_split(unsigned char* hi, unsigned char* lo, int r, const float* x) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        float h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = tf32_hi(x[4 * c + q]);
+            l[q] = x[4 * c + q] - h[q];
+        }
+        const int o = r * 128 + ((c ^ (r & 7)) << 4);
+        *reinterpret_cast<float4*>(hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;   // 0.2 s for a few microseconds of MMA work
+
+template <int P, bool MASS>
+__global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(const CellMatArgs a) {
+    using G = CmGeo<P>;
+    constexpr int N = G::N, NP = G::NP, NPN = G::NPN, N3 = G::N3, L = G::L, NPAD = G::NPAD;
+    constexpr int CH = G::CH, MAXCH = G::MAXCH, KSTEPS = G::KSTEPS, KCH = (8 * KSTEPS) / 4;
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    unsigned char* sm = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
+    float* U = reinterpret_cast<float*>(sm + G::OFF_U);    // gathered patch tensor, then the cells' results
+    float* Vs = reinterpret_cast<float*>(sm + G::OFF_V);   // [8][N3]
+    __shared__ int32_t sOff[kUnitBlocks][8];
+    __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
+    __shared__ int sChB[MAXCH], sChC[MAXCH], sNch, sTen, sMagic;
+    __shared__ int sNode[NPN];
+    __shared__ int64_t sItem;
+    __shared__ __align__(8) uint64_t sBar;
+    __shared__ uint32_t sTmem;
+    __shared__ int sFail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t bar = smem_u32(&sBar);
+
+    // ---- constant operand tiles (pre-swizzled), tensor memory, barrier ------
+    {
+        const unsigned dst = smem_u32(sm + G::OFF_B1H);
+        for (int e = tid; e < G::SET_FLOATS / 4; e += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16u * e), "l"(a.consts + 4 * e)
+                         : "memory");
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        fence_async_smem();                               // the tiles feed the tensor cores
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sTmem)),
+                     "r"(G::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sFail = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sTmem;
+    uint32_t phase = 0;
+
+    // row of this thread: tile t, row r; its accumulators in tensor memory
+    const int t = tid >> 7, r = tid & 127;
+    unsigned char* aHi = sm + G::OFF_AH + t * G::TILE;
+    unsigned char* aLo = sm + G::OFF_AL + t * G::TILE;
+    const uint32_t tD = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(t * 2 * NPAD);
+    const int cell = tid / L, lane = tid % L;
+    const int cx = cell & 1, cy = (cell >> 1) & 1, cz = (cell >> 2) & 1;
+
+    if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);
+    __syncthreads();
+    int64_t item = sItem;
+    while (item < a.n_units) {
+        const Unit& unit = a.units[item];
+        const int px = unit.pxyz & 1023, py = (unit.pxyz >> 10) & 1023, pz = unit.pxyz >> 20;
+        // work-list check, as in the register kernel
+        bool unit_ok = unit.nb >= 1 && unit.nb <= kUnitBlocks;
+        if (unit_ok) {
+            int lds = 0, lanes = 0;
+            for (int q = 0; q < unit.nb; ++q) {
+                const int wq = unit.width[q], lq = unit.ld[q];
+                unit_ok = unit_ok && wq >= 1 && wq <= lq && lq % CH == 0;
+                lds += lq;
+                lanes += wq;
+            }
+            unit_ok = unit_ok && lds <= kUnitLdSum && lanes <= L;
+        }
+        if (!unit_ok && tid == 0) atomicExch(a.status, kDevBadTile);
+        if (unit_ok) {
+            // ---- unit tables ------------------------------------------------
+            if (tid < L) {
+                int b = -1, col = 0, pref = 0;
+                for (int q = 0; q < unit.nb; ++q) {
+                    const int wq = unit.width[q];
+                    if (tid >= pref && tid < pref + wq) { b = q; col = tid - pref; }
+                    pref += wq;
+                }
+                sLaneB[tid] = b;
+                sLaneA[tid] = col;
+                sOff[tid >> 3][tid & 7] = (tid >> 3) < unit.nb ? unit.off[tid >> 3][tid & 7] : -1;
+            }
+            if (tid == 0) {
+                int base = 0, nch = 0;
+                for (int q = 0; q < kUnitBlocks; ++q) {
+                    const int ldq = q < unit.nb ? unit.ld[q] : 0;
+                    sBase[q] = base;
+                    sLd[q] = ldq;
+                    sMask[q] = q < unit.nb ? unit.cellmask[q] : 0;
+                    for (int c0 = 0; c0 < ldq; c0 += CH) { sChB[nch] = q; sChC[nch] = c0; ++nch; }
+                    base += NPN * ldq;
+                }
+                sNch = nch;
+                sTen = base;
+                sMagic = (65536 + nch - 1) / nch;     // e / nch == (e * sMagic) >> 16 for e < NPN * nch
+            }
+            for (int n = tid; n < NPN; n += blockDim.x) sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
+            __syncthreads();
+
+            const int nch = sNch, magic = sMagic, ntask = NPN * nch;
+            // ---- gather -----------------------------------------------------
+            {
+                const unsigned ubase = smem_u32(U);
+                for (int e = tid; e < ntask; e += blockDim.x) {
+                    const int node = (e * magic) >> 16, j = e - node * nch;
+                    const int b = sChB[j], c0 = sChC[j], ld = sLd[b];
+                    const int ne = sNode[node];
+                    const int32_t o = ne >= 0 ? sOff[b][ne >> 16] : -1;
+                    const bool ok = o >= 0;
+                    const float* src = ok ? a.P + (int64_t)o * 4 + (ne & 0xffff) * ld + c0 : a.P;
+                    const unsigned dst = ubase + (unsigned)((sBase[b] + node * ld + c0) * 4);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                                 "r"(ok ? 16 : 0) : "memory");
+                }
+                if constexpr (!MASS) {
+                    const float* Vg = a.Vq + (int64_t)unit.patch * 8 * N3;
+                    const unsigned vbase = smem_u32(Vs);
+                    for (int e = tid; e < 8 * N3 / CH; e += blockDim.x)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(vbase + 16u * e),
+                                     "l"(Vg + e * CH)
+                                     : "memory");
+                }
+                asm volatile("cp.async.wait_all;\n" ::: "memory");
+            }
+            __syncthreads();
+
+            // ---- stage 1 operand: the thread's cell-column at its cell's nodes
+            const int b = sLaneB[lane];
+            const bool act = b >= 0 && ((sMask[b] >> cell) & 1);
+            const int ld = act ? sLd[b] : 0;
+            const int base = act ? sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * ld : 0;
+            {
+                float x[4 * KCH];
+#pragma unroll
+                for (int k = 0; k < 4 * KCH; ++k) x[k] = 0.f;
+                if (act) {
+#pragma unroll
+                    for (int z = 0; z < N; ++z)
+#pragma unroll
+                        for (int y = 0; y < N; ++y)
+#pragma unroll
+                            for (int xx = 0; xx < N; ++xx)
+                                x[(z * N + y) * N + xx] = U[base + ((z * NP + y) * NP + xx) * ld];
+                }
+                store_row_split<KCH>(aHi, aLo, r, x);
+            }
+            fence_async_smem();
+            __syncthreads();                              // A complete; the patch tensor is free
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t id1 = tf32_idesc(128, MASS ? NPAD : 2 * NPAD);
+#pragma unroll
+                for (int tt = 0; tt < 2; ++tt) {
+                    const uint32_t d = tmem + (uint32_t)(tt * 2 * NPAD);
+                    const uint32_t ah = smem_u32(sm + G::OFF_AH + tt * G::TILE), al = smem_u32(sm + G::OFF_AL + tt * G::TILE);
+                    const uint32_t bh = smem_u32(sm + G::OFF_B1H), bl = smem_u32(sm + G::OFF_B1L);
+#pragma unroll
+                    for (int kk = 0; kk < KSTEPS; ++kk) {
+                        mma_tf32(d, sw128_desc(ah + 32 * kk), sw128_desc(bh + 32 * kk), id1, kk > 0);
+                        mma_tf32(d, sw128_desc(ah + 32 * kk), sw128_desc(bl + 32 * kk), id1, 1);
+                        mma_tf32(d, sw128_desc(al + 32 * kk), sw128_desc(bh + 32 * kk), id1, 1);
+                    }
+                }
+                mma_commit(bar);
+            }
+            // zero the patch tensor for the results while the MMAs run
+            const int ten4 = sTen / CH;
+            for (int e = tid; e < ten4; e += blockDim.x) reinterpret_cast<uint4*>(U)[e] = make_uint4(0u, 0u, 0u, 0u);
+            if (tid == 0 && !mbar_wait(bar, phase, kWaitLimitNs)) sFail = 1;
+            phase ^= 1;
+            __syncthreads();
+            if (sFail) break;
+            tc_fence_after();
+
+            if constexpr (!MASS) {
+                // ---- stage 2 operand: |J| V o u_q (|J| is in Sb3) -----------
+                float uq[NPAD];
+                tmem_load<NPAD>(tD + NPAD, uq);
+                float x[4 * KCH];
+#pragma unroll
+                for (int k = 0; k < 4 * KCH; ++k) x[k] = k < N3 ? uq[k] * Vs[cell * N3 + k] : 0.f;
+                store_row_split<KCH>(aHi, aLo, r, x);
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint32_t id2 = tf32_idesc(128, NPAD);
+#pragma unroll
+                    for (int tt = 0; tt < 2; ++tt) {
+                        const uint32_t d = tmem + (uint32_t)(tt * 2 * NPAD);
+                        const uint32_t ah = smem_u32(sm + G::OFF_AH + tt * G::TILE), al = smem_u32(sm + G::OFF_AL + tt * G::TILE);
+                        const uint32_t bh = smem_u32(sm + G::OFF_B2H), bl = smem_u32(sm + G::OFF_B2L);
+#pragma unroll
+                        for (int kk = 0; kk < KSTEPS; ++kk) {
+                            mma_tf32(d, sw128_desc(ah + 32 * kk), sw128_desc(bh + 32 * kk), id2, 1);
+                            mma_tf32(d, sw128_desc(ah + 32 * kk), sw128_desc(bl + 32 * kk), id2, 1);
+                            mma_tf32(d, sw128_desc(al + 32 * kk), sw128_desc(bh + 32 * kk), id2, 1);
+                        }
+                    }
+                    mma_commit(bar);
+                    if (!mbar_wait(bar, phase, kWaitLimitNs)) sFail = 1;
+                }
+                phase ^= 1;
+                __syncthreads();
+                if (sFail) break;
+                tc_fence_after();
+            }
+
+            // ---- the cell's result into the patch tensor ---------------------
+            {
+                float y[NPAD];
+                tmem_load<NPAD>(tD, y);
+                if (act) {
+#pragma unroll
+                    for (int z = 0; z < N; ++z)
+#pragma unroll
+                        for (int yy = 0; yy < N; ++yy)
+#pragma unroll
+                            for (int xx = 0; xx < N; ++xx)
+                                atomicAdd(&U[base + ((z * NP + yy) * NP + xx) * ld], y[(z * N + yy) * N + xx]);
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+
+            // ---- scatter-add of 16-byte chunks --------------------------------
+            for (int e = tid; e < ntask; e += blockDim.x) {
+                const int node = (e * magic) >> 16, j = e - node * nch;
+                const int ne = sNode[node];
+                if (ne < 0) continue;
+                const int bb = sChB[j];
+                const int32_t o = sOff[bb][ne >> 16];
+                if (o < 0) continue;
+                const int c0 = sChC[j], ldb = sLd[bb];
+                const float4 f = *reinterpret_cast<const float4*>(U + sBase[bb] + node * ldb + c0);
+                const float v[4] = {f.x, f.y, f.z, f.w};
+                if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f)
+                    red_chunk(a.Y + (int64_t)o * 4 + (ne & 0xffff) * ldb + c0, v);
+            }
+        }  // unit_ok
+        __syncthreads();                                  // shared tables are rebuilt for the next unit
+        if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);
+        __syncthreads();
+        item = sItem;
+    }
+
+    // ---- teardown: on a time-out, give the MMAs in flight one more bounded
+    // wait; then release the tensor memory ----------------------------------
+    if (sFail) {
+        if (tid == 0) {
+            atomicExch(a.status, kDevTimeout);
+            mbar_wait(bar, phase ^ 1, kWaitLimitNs);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+template <int P>
+cudaError_t launch_cellmat_p(const CellMatArgs& a, cudaStream_t s) {
+    using G = CmGeo<P>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(apply_cellmat_kernel<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(apply_cellmat_kernel<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (a.n_units == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min<int64_t>(a.n_units, (int64_t)sms * 2);
+    if (a.mass)
+        apply_cellmat_kernel<P, true><<<grid, G::THREADS, G::bytes, s>>>(a);
+    else
+        apply_cellmat_kernel<P, false><<<grid, G::THREADS, G::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_apply_cellmat(int p, const CellMatArgs& a, cudaStream_t s) {
+    switch (p) {
+        case 1: return launch_cellmat_p<1>(a, s);
+        case 2: return launch_cellmat_p<2>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace femf

@@ -177,6 +177,31 @@ struct ApplyUnitArgs {
 };
 template <typename T>
 cudaError_t launch_apply_units(int p, const ApplyUnitArgs<T>& a, cudaStream_t s);
+
+// Cell-matrix form of the apply (apply_cellmat.cu; p <= 2, FP32, tensor
+// cores).  Constant operands per operator ("set"): B1 = [K_L; S3] (H) or
+// [M_c; 0] (M), 2 npad rows, and B2 = Sb3 with |J| (H) or 0 (M), npad rows;
+// each row holds 32 FP32 values (cell nodes or Gauss points, zero-padded) in
+// the 128-byte-swizzled K-major tile layout of the kernel's shared memory:
+// element (r, k) at float index 32 r + 4 ((k / 4) ^ (r % 8)) + k % 4.  A set
+// is B1 high, B1 low, B2 high, B2 low, the high part the TF32 rounding of
+// the matrix and the low part the FP32 remainder.
+constexpr int cellmat_npad(int p) { return p == 1 ? 16 : 32; }
+constexpr int cellmat_set_floats(int p) { return 6 * cellmat_npad(p) * 32; }
+struct CellMatArgs {
+    const float* P;
+    float* Y;
+    const float* Vq;
+    const Unit* units;
+    int64_t n_units;
+    unsigned long long* ticket;   // work counter, zeroed before the launch (CTAs are persistent)
+    int32_t lx, ly, lz;
+    int32_t dirichlet;
+    int32_t* status;
+    int32_t mass;                 // 1: the mass operator (stage 1 only, Vq unused)
+    const float* consts;          // the operator's constant set (16-byte aligned, device)
+};
+cudaError_t launch_apply_cellmat(int p, const CellMatArgs& a, cudaStream_t s);
 template <typename T>
 size_t apply_smem_bytes(int p, int wmax, int ldmax, int cells_per_round);
 template <typename T>
@@ -241,6 +266,7 @@ cudaError_t probe_fma_static(int dtype, int64_t iters, double* flops_per_s, cuda
 enum DeviceStatus : int32_t {
     kDevOk = 0,
     kDevBadTile = 1,
+    kDevTimeout = 2,      // a bounded wait on the tensor cores ran out
 };
 
 }  // namespace femf

@@ -121,6 +121,9 @@ struct fe_mesh {
     std::vector<double> gll, gx, gw;
     CellConsts<double> kd;
     CellConsts<float> kf;
+    // cell-matrix form (p <= 2): constant operand sets for H and M, copied
+    // into the workspace after the status word
+    std::vector<float> cm_host;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int32_t* status = nullptr;
@@ -200,6 +203,7 @@ struct fe_bcsr {
     // launch configuration of the apply (set by fe_bcsr_set_launch / fe_autotune)
     int32_t persistent = 0, ctas_per_sm = 4, cells_per_round = 0;
     int32_t closed = 0;   // the caller declares the pattern closed for P's values (fe_bcsr_set_closed)
+    int32_t form = 0;     // FE_FORM_SUMFAC or FE_FORM_CELLMAT (fe_bcsr_set_form)
     int64_t active_cell_cols = 0;
     double gram_flops = 0.0;
     uint64_t fingerprint = 0;
@@ -217,6 +221,83 @@ struct fe_bcsr {
 };
 
 namespace {
+
+// TF32 rounding of x (to nearest, ties away from zero): the high part of
+// the split used by the cell-matrix kernel; the low part is x minus it.
+float tf32_round(double x) {
+    float f = float(x);
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    b = (b + 0x1000u) & ~0x1FFFu;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+// Constant operands of the cell-matrix form (Sec. 3.2, Eq.
+// fe_matrices_cell_based, element matrices of a cell of the box mesh), in
+// FP64 from the 1D tables, then split and laid out as the kernel's tiles.
+// Cell-local index a = ax + n (ay + n az) for nodes and Gauss points alike.
+//   S3[q][a]  = S[qx][ax] S[qy][ay] S[qz][az]           values at the Gauss points
+//   Sb3[a][q] = Sb[ax][qx] Sb[ay][qy] Sb[az][qz]       weighted transpose
+//   L_c[q][r] = sum_d A_d along direction d (identity in the other two)
+//   K_L = Sb3 L_c S3,  Sb3J = |J| Sb3,  M_c = Sb3J S3
+// (A_d already carries |J| / (2 h_d^2)).  Set H: B1 = [K_L; S3], B2 = Sb3J;
+// set M: B1 = [M_c; 0], B2 = 0.
+void build_cellmat_consts(fe_mesh& m) {
+    const int n = m.p + 1, n3 = n * n * n, npad = cellmat_npad(m.p);
+    const CellConsts<double>& k = m.kd;
+    std::vector<double> S3(n3 * n3), Sb3(n3 * n3), Lc(n3 * n3, 0.0), T(n3 * n3), KL(n3 * n3), Sb3J(n3 * n3), Mc(n3 * n3);
+    auto co = [n](int i, int d) { return d == 0 ? i % n : (d == 1 ? (i / n) % n : i / (n * n)); };
+    for (int q = 0; q < n3; ++q)
+        for (int a = 0; a < n3; ++a) {
+            S3[q * n3 + a] = k.S[co(q, 0)][co(a, 0)] * k.S[co(q, 1)][co(a, 1)] * k.S[co(q, 2)][co(a, 2)];
+            Sb3[q * n3 + a] = k.Sb[co(q, 0)][co(a, 0)] * k.Sb[co(q, 1)][co(a, 1)] * k.Sb[co(q, 2)][co(a, 2)];
+            for (int d = 0; d < 3; ++d) {
+                bool same = true;
+                for (int e = 0; e < 3; ++e)
+                    if (e != d && co(q, e) != co(a, e)) same = false;
+                if (same) Lc[q * n3 + a] += k.A[d][co(q, d)][co(a, d)];
+            }
+        }
+    auto matmul = [n3](const std::vector<double>& X, const std::vector<double>& Y, std::vector<double>& Z) {
+        for (int i = 0; i < n3; ++i)
+            for (int j = 0; j < n3; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < n3; ++l) s += X[i * n3 + l] * Y[l * n3 + j];
+                Z[i * n3 + j] = s;
+            }
+    };
+    matmul(Lc, S3, T);
+    matmul(Sb3, T, KL);
+    for (int i = 0; i < n3 * n3; ++i) Sb3J[i] = k.jxw * Sb3[i];
+    matmul(Sb3J, S3, Mc);
+    const int set = cellmat_set_floats(m.p);
+    m.cm_host.assign(2 * (size_t)set, 0.f);
+    // rows of `rows` x 32 floats starting at tile, element (r, kk) swizzled
+    auto put = [](float* tile, int r, int kk, float v) { tile[32 * r + 4 * ((kk / 4) ^ (r % 8)) + kk % 4] = v; };
+    auto fill = [&](float* s0, const std::vector<double>* b1top, const std::vector<double>* b1bot,
+                    const std::vector<double>* b2) {
+        float* b1h = s0;
+        float* b1l = b1h + 2 * npad * 32;
+        float* b2h = b1l + 2 * npad * 32;
+        float* b2l = b2h + npad * 32;
+        for (int r = 0; r < n3; ++r)
+            for (int kk = 0; kk < n3; ++kk) {
+                const double parts[3] = {b1top ? (*b1top)[r * n3 + kk] : 0.0, b1bot ? (*b1bot)[r * n3 + kk] : 0.0,
+                                         b2 ? (*b2)[r * n3 + kk] : 0.0};
+                float* hi[3] = {b1h, b1h, b2h};
+                float* lo[3] = {b1l, b1l, b2l};
+                const int row[3] = {r, npad + r, r};
+                for (int w = 0; w < 3; ++w) {
+                    const float h = tf32_round(parts[w]);
+                    put(hi[w], row[w], kk, h);
+                    put(lo[w], row[w], kk, float(parts[w] - double(h)));
+                }
+            }
+    };
+    fill(m.cm_host.data(), &KL, &S3, &Sb3J);
+    fill(m.cm_host.data() + set, &Mc, nullptr, nullptr);
+}
 
 void build_consts(fe_mesh& m) {
     const int p = m.p, n = p + 1;
@@ -270,6 +351,7 @@ void build_consts(fe_mesh& m) {
             for (int d = 0; d < 3; ++d) f.A[d][i][j] = float(k.A[d][i][j]);
         }
     f.jxw = float(k.jxw);
+    if (p <= 2) build_cellmat_consts(m);
 }
 
 uint64_t hash_mix(uint64_t h, uint64_t v) {
@@ -432,15 +514,20 @@ int fe_mesh_quad_points(const fe_mesh* m, double* xyz) {
 
 int fe_mesh_workspace_bytes(const fe_mesh* m, size_t* bytes) {
     if (!m || !bytes) return fail(FE_EINVAL, "fe_mesh_workspace_bytes: NULL argument");
-    *bytes = 256;
+    *bytes = 256 + m->cm_host.size() * sizeof(float);
     return FE_OK;
 }
 
 int fe_mesh_upload(fe_mesh* m, void* ws, size_t bytes, void* stream) {
     if (!m || !ws) return fail(FE_EINVAL, "fe_mesh_upload: NULL argument");
-    if (bytes < 256) return fail(FE_ENOMEM, "fe_mesh_upload: workspace of %zu bytes is below the 256 needed", bytes);
+    const size_t need = 256 + m->cm_host.size() * sizeof(float);
+    if (bytes < need) return fail(FE_ENOMEM, "fe_mesh_upload: workspace of %zu bytes is below the %zu needed", bytes, need);
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(FE_EINVAL, "fe_mesh_upload: workspace must be 256-byte aligned");
     FE_TRY_CUDA(cudaMemsetAsync(ws, 0, 256, (cudaStream_t)stream), "fe_mesh_upload: cudaMemsetAsync");
+    if (!m->cm_host.empty())
+        FE_TRY_CUDA(cudaMemcpyAsync(static_cast<char*>(ws) + 256, m->cm_host.data(), m->cm_host.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, (cudaStream_t)stream),
+                    "fe_mesh_upload: constants");
     m->ws = ws;
     m->ws_bytes = bytes;
     m->status = reinterpret_cast<int32_t*>(ws);
@@ -982,6 +1069,23 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool ma
     if constexpr (sizeof(T) == 8) a.k = m->kd; else a.k = m->kf;
     if (Y->n_values == 0) return FE_OK;                       // empty pattern: nothing to compute
     FE_TRY_CUDA(cudaMemsetAsync(Y->values, 0, (size_t)Y->n_values * sizeof(T), s), "fe_apply_H: zero Y");
+    if constexpr (sizeof(T) == 4) {
+        if (P->form == FE_FORM_CELLMAT && m->p <= 2) {
+            CellMatArgs c;
+            c.P = a.P; c.Y = a.Y; c.Vq = a.Vq;
+            c.units = reinterpret_cast<const Unit*>(static_cast<const char*>(P->tables) + P->off_units);
+            c.n_units = (int64_t)P->units.size();
+            c.ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(P->tables) + P->off_ticket);
+            FE_TRY_CUDA(cudaMemsetAsync(c.ticket, 0, sizeof(unsigned long long), s), "fe_apply_H: reset work counter");
+            c.lx = a.lx; c.ly = a.ly; c.lz = a.lz; c.dirichlet = a.dirichlet;
+            c.status = a.status;
+            c.mass = a.mass;
+            c.consts = reinterpret_cast<const float*>(static_cast<const char*>(m->ws) + 256) +
+                       (mass ? cellmat_set_floats(m->p) : 0);
+            FE_TRY_CUDA(launch_apply_cellmat(m->p, c, s), "fe_apply_H: cell-matrix kernel launch");
+            return FE_OK;
+        }
+    }
     if (m->p <= 2) {
         ApplyUnitArgs<T> u;
         u.P = a.P; u.Y = a.Y; u.Vq = a.Vq;
@@ -1172,6 +1276,22 @@ int fe_bcsr_set_launch(fe_bcsr* b, int32_t persistent, int32_t ctas_per_sm, int3
     b->persistent = persistent;
     b->ctas_per_sm = ctas_per_sm;
     b->cells_per_round = cells_per_round;
+    return FE_OK;
+}
+
+int fe_bcsr_set_form(fe_bcsr* b, int32_t form) {
+    if (!b) return fail(FE_EINVAL, "fe_bcsr_set_form: NULL multivector");
+    if (form != FE_FORM_SUMFAC && form != FE_FORM_CELLMAT)
+        return fail(FE_EINVAL, "fe_bcsr_set_form: form must be FE_FORM_SUMFAC or FE_FORM_CELLMAT");
+    if (form == FE_FORM_CELLMAT && (b->dtype != FE_F32 || !b->mesh || b->mesh->p > 2))
+        return fail(FE_EUNSUPPORTED, "fe_bcsr_set_form: the cell-matrix form needs FE_F32 values and p <= 2");
+    b->form = form;
+    return FE_OK;
+}
+
+int fe_bcsr_get_form(const fe_bcsr* b, int32_t* form) {
+    if (!b || !form) return fail(FE_EINVAL, "fe_bcsr_get_form: NULL argument");
+    *form = b->form;
     return FE_OK;
 }
 

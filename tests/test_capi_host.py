@@ -195,3 +195,32 @@ def test_closed_flag(lib):
     assert b.get_closed() is True
     from paper_1907_01005_gb300 import _capi
     assert _capi.fe_bcsr_set_closed(b.h, 2) == _capi.FE_EINVAL
+
+
+def test_form_knob(lib):
+    """The cell-matrix form is accepted for FP32 at p <= 2 only; the mesh
+    workspace grows by its constant operand sets (2 sets x 6 npad x 32 floats)."""
+    import ctypes as C
+    from paper_1907_01005_gb300 import BCSR, FORM_CELLMAT, FORM_SUMFAC, FeError, Mesh, _capi
+    for p, npad in [(1, 16), (2, 32)]:
+        m = Mesh(4, 4, 4, 1, 1, 1, p)
+        nb = C.c_size_t()
+        _capi.check(_capi.fe_mesh_workspace_bytes(m.h, C.byref(nb)))
+        assert nb.value == 256 + 2 * 6 * npad * 32 * 4
+        R = m.n_row_blocks
+        b = BCSR(m, np.array([0, 8], np.int32), np.arange(R + 1, dtype=np.int64), np.zeros(R, np.int32), 1)
+        assert b.get_form() == FORM_SUMFAC
+        b.set_form(FORM_CELLMAT)
+        assert b.get_form() == FORM_CELLMAT
+        assert _capi.fe_bcsr_set_form(b.h, 2) == _capi.FE_EINVAL
+        assert b.get_form() == FORM_CELLMAT
+        b64 = BCSR(m, np.array([0, 8], np.int32), np.arange(R + 1, dtype=np.int64), np.zeros(R, np.int32), 2)
+        assert _capi.fe_bcsr_set_form(b64.h, FORM_CELLMAT) == _capi.FE_EUNSUPPORTED
+    m4 = Mesh(2, 2, 2, 1, 1, 1, 4)
+    nb = C.c_size_t()
+    _capi.check(_capi.fe_mesh_workspace_bytes(m4.h, C.byref(nb)))
+    assert nb.value == 256
+    R = m4.n_row_blocks
+    b4 = BCSR(m4, np.array([0, 8], np.int32), np.arange(R + 1, dtype=np.int64), np.zeros(R, np.int32), 1)
+    with pytest.raises(FeError, match="p <= 2"):
+        b4.set_form(FORM_CELLMAT)
