@@ -255,9 +255,12 @@ int fe_apply_H_gram(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_PY_de
 
 /* End-to-end variant for callers whose data lives in host memory: copies
  * P's values from P_host (value_bytes) into P's bound device array, runs
- * fe_apply_H_gram, copies Y's values to Y_host and both Gram matrices to
- * G_PY_host / G_PP_host, and synchronises `stream`.  Host buffers should be
- * pinned for full copy bandwidth. */
+ * the step of fe_apply_H_gram, copies Y's values to Y_host and both Gram
+ * matrices to G_PY_host / G_PP_host, and synchronises `stream`.  The copies
+ * overlap the kernels where the data allows: G_PP leaves on P's side stream
+ * after P^T P, and Y leaves on a second stream owned by P (created on the
+ * first call, destroyed with P) while P^T Y runs.  Host buffers should be
+ * pinned for full copy bandwidth and for the copies to run asynchronously. */
 int fe_apply_H_gram_host(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_PY_dev,
                          double* G_PP_dev, const void* P_host, void* Y_host,
                          double* G_PY_host, double* G_PP_host, void* stream);
@@ -269,13 +272,15 @@ int fe_apply_H_gram_host(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_
  * multivectors' column order.  The truncation of Alg. 7: products A_rk X_kj
  * whose column block j is not stored in row block r are discarded.  FP32
  * multivectors compute with X rounded to FP32 and FP32 FMAs (the result is
- * FP32); FP64 ones in FP64.  C's row padding is written as zero.  C must
- * be bound with a table buffer (its pattern tables are used); A needs values
- * only.  C may not alias A (FE_EINVAL).  With gamma the orbital-minimisation gradient of Sec. 2,
+ * FP32); FP64 ones in FP64.  C's row padding is written as zero; A's row
+ * padding must hold finite values (every routine here writes zeros there).
+ * C must be bound with a table buffer: its pattern tables are used, and for
+ * FP32 the rounded copy of X is written into it (so calls with the same C
+ * must not overlap).  A needs values only.  C may not alias A (FE_EINVAL).  With gamma the orbital-minimisation gradient of Sec. 2,
  * G = -2 Phi_M Hbar + 2 Phi_H (2 I - Mbar), is
  *   fe_mmult(Phi_H, Mbar, -2, -2, 0, G);  fe_mmult(Phi_M, Hbar, -2, 0, 1, G).
- * FE_EUNSUPPORTED if a row block's stored blocks hold more than 6144
- * columns. */
+ * FE_EUNSUPPORTED if the row strides of a row block's stored blocks add up
+ * to more than 6144 columns. */
 int fe_mmult(const fe_bcsr* A, const double* X_dev, double alpha, double gamma, double beta, fe_bcsr* C,
              void* stream);
 

@@ -221,8 +221,9 @@ struct MmultArgs {
     const T* A;
     T* C;
     const double* X;            // M x M, row-major, the multivectors' column order
+    const T* Xw;                // X in the working precision (set by launch_mmult)
     int32_t n_cols;
-    int32_t wmax_union;         // largest union (columns of a row block's stored blocks)
+    int32_t wmax_union;         // largest padded union (row strides of a row block's stored blocks)
     const MmultItem* items;
     int64_t n_items;
     const int64_t* row_ptr;     // BCSR pattern on the device
@@ -231,8 +232,8 @@ struct MmultArgs {
     const int32_t* cbp;
     const int32_t* ld;
     const int32_t* rb_rows;
-    const int32_t* ucol0;       // first union column of each stored block within its row block
-    const int32_t* rb_union;    // union columns of each row block
+    const int32_t* ucol0;       // first padded-union column of each stored block within its row block
+    const int32_t* rb_union;    // padded-union columns of each row block
     double alpha, gamma, beta;
     int32_t* status;
 };
@@ -251,8 +252,11 @@ struct TraceArgs {
 };
 template <typename T>
 size_t mmult_smem_bytes(int wmax_union);
+// Dynamic shared memory the post-multiplication may use (two k-tile buffers
+// and the union tables); x_round (FP32 only) receives X rounded to FP32.
+constexpr size_t kMmultSmemMax = 200 * 1024;
 template <typename T>
-cudaError_t launch_mmult(const MmultArgs<T>& a, cudaStream_t s);
+cudaError_t launch_mmult(const MmultArgs<T>& a, float* x_round, cudaStream_t s);
 template <typename T>
 cudaError_t launch_trace(const TraceArgs<T>& a, cudaStream_t s);
 

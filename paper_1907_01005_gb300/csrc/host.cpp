@@ -196,7 +196,7 @@ struct fe_bcsr {
     std::vector<int32_t> block_rb, rb_rows, ucol0, rb_union;
     int32_t wmax_union = 0;
     size_t off_rowptr = 0, off_colidx = 0, off_blkoff = 0, off_blockrb = 0, off_rbrows = 0, off_mmitems = 0;
-    size_t off_ucol0 = 0, off_rbunion = 0;
+    size_t off_ucol0 = 0, off_rbunion = 0, off_xround = 0;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
     size_t off_tcg = 0, off_tcpy = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
     size_t off_units = 0, off_ld = 0, off_ticket = 0;
@@ -213,10 +213,16 @@ struct fe_bcsr {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t elem() const { return dtype == FE_F64 ? 8 : 4; }
+    // copy stream of fe_apply_H_gram_host (Y goes back to the host while P^T Y runs)
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_y = nullptr, ev_copied = nullptr;
     ~fe_bcsr() {
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (side) cudaStreamDestroy(side);
+        if (ev_y) cudaEventDestroy(ev_y);
+        if (ev_copied) cudaEventDestroy(ev_copied);
+        if (copy) cudaStreamDestroy(copy);
     }
 };
 
@@ -879,7 +885,8 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
             b->tc_rows.resize(R);
             for (int rr = 0; rr < R; ++rr) b->tc_rows[rr] = int32_t(m->rb_ptr[rr + 1] - m->rb_ptr[rr]);
         }
-        // ---- post-multiplication items: (row block, 64-row chunk, 64-column chunk)
+        // ---- post-multiplication items: (row block, 64-row chunk, 128-column
+        // chunk of the padded union: each stored block contributes its row stride)
         b->rb_rows.resize(R);
         b->rb_union.resize(R);
         b->block_rb.resize(nnz);
@@ -891,12 +898,12 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
             for (int64_t k = row_ptr[rr]; k < row_ptr[rr + 1]; ++k) {
                 b->block_rb[k] = rr;
                 b->ucol0[k] = W;
-                W += cbp[col_idx[k] + 1] - cbp[col_idx[k]];
+                W += b->ld[col_idx[k]];
             }
             b->rb_union[rr] = W;
             b->wmax_union = std::max(b->wmax_union, W);
             for (int i0 = 0; W > 0 && i0 < rows; i0 += 64)
-                for (int j0 = 0; j0 < W; j0 += 64) b->mm_items.push_back(MmultItem{rr, i0, j0, 0});
+                for (int j0 = 0; j0 < W; j0 += 128) b->mm_items.push_back(MmultItem{rr, i0, j0, 0});
         }
         size_t off = 0;
         b->off_tiles = off; off = align_up(off + b->tiles.size() * sizeof(Tile), 256);
@@ -923,6 +930,8 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_mmitems = off; off = align_up(off + b->mm_items.size() * sizeof(MmultItem), 256);
         b->off_ucol0 = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int32_t), 256);
         b->off_rbunion = off; off = align_up(off + R * sizeof(int32_t), 256);
+        // X of fe_mmult rounded to FP32 (FE_F32 multivectors)
+        b->off_xround = off; off = align_up(off + (dtype == FE_F32 ? (size_t)n_cols * n_cols * sizeof(float) : 16), 256);
         b->table_bytes = off;
     } catch (const std::bad_alloc&) {
         delete b;
@@ -1201,17 +1210,26 @@ int fe_gram_PtP(const fe_bcsr* P, double* G, void* stream) {
     return P->dtype == FE_F64 ? gram_impl<double>(P, P, true, G, s) : gram_impl<float>(P, P, true, G, s);
 }
 
+namespace {
+// P's side stream and its fork/join events, created on first use
+int ensure_side(fe_bcsr* Pm) {
+    if (!Pm->side) {
+        FE_TRY_CUDA(cudaStreamCreateWithFlags(&Pm->side, cudaStreamNonBlocking), "fe_apply_H_gram: side stream");
+        FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_fork, cudaEventDisableTiming), "fe_apply_H_gram: event");
+        FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_join, cudaEventDisableTiming), "fe_apply_H_gram: event");
+    }
+    return FE_OK;
+}
+}  // namespace
+
 int fe_apply_H_gram(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY, double* G_PP, void* stream) {
     int rc = check_pair("fe_apply_H_gram", m, P, Y);
     if (rc) return rc;
     // P^T P does not depend on Y: it runs on P's side stream, forked from and
     // joined back into `stream` with events (a pattern stream capture keeps)
     fe_bcsr* Pm = const_cast<fe_bcsr*>(P);
-    if (!Pm->side) {
-        FE_TRY_CUDA(cudaStreamCreateWithFlags(&Pm->side, cudaStreamNonBlocking), "fe_apply_H_gram: side stream");
-        FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_fork, cudaEventDisableTiming), "fe_apply_H_gram: event");
-        FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_join, cudaEventDisableTiming), "fe_apply_H_gram: event");
-    }
+    rc = ensure_side(Pm);
+    if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     FE_TRY_CUDA(cudaEventRecord(Pm->ev_fork, s), "fe_apply_H_gram: fork");
     FE_TRY_CUDA(cudaStreamWaitEvent(Pm->side, Pm->ev_fork, 0), "fe_apply_H_gram: fork");
@@ -1228,17 +1246,40 @@ int fe_apply_H_gram_host(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY,
     if (!P_host || !Y_host || !G_PY_host || !G_PP_host) return fail(FE_EINVAL, "fe_apply_H_gram_host: NULL host buffer");
     int rc = check_pair("fe_apply_H_gram_host", m, P, Y);
     if (rc) return rc;
+    fe_bcsr* Pm = const_cast<fe_bcsr*>(P);
+    rc = ensure_side(Pm);
+    if (rc) return rc;
+    if (!Pm->copy) {
+        FE_TRY_CUDA(cudaStreamCreateWithFlags(&Pm->copy, cudaStreamNonBlocking), "fe_apply_H_gram_host: copy stream");
+        FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_y, cudaEventDisableTiming), "fe_apply_H_gram_host: event");
+        FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_copied, cudaEventDisableTiming), "fe_apply_H_gram_host: event");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vb = (size_t)P->n_values * P->elem();
     const size_t gb = (size_t)P->n_cols * P->n_cols * sizeof(double);
+    // P in; then P^T P (and its copy out) on the side stream beside the apply;
+    // Y out on the copy stream while P^T Y runs; G_PY out on `stream`
     FE_TRY_CUDA(cudaMemcpyAsync(P->values, P_host, vb, cudaMemcpyHostToDevice, s), "fe_apply_H_gram_host: copy P in");
-    rc = fe_apply_H_gram(m, P, Y, G_PY, G_PP, stream);
-    if (rc) return rc;
-    FE_TRY_CUDA(cudaMemcpyAsync(Y_host, Y->values, vb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy Y out");
-    FE_TRY_CUDA(cudaMemcpyAsync(G_PY_host, G_PY, gb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy G_PY out");
-    FE_TRY_CUDA(cudaMemcpyAsync(G_PP_host, G_PP, gb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy G_PP out");
+    FE_TRY_CUDA(cudaEventRecord(Pm->ev_fork, s), "fe_apply_H_gram_host: fork");
+    FE_TRY_CUDA(cudaStreamWaitEvent(Pm->side, Pm->ev_fork, 0), "fe_apply_H_gram_host: fork");
+    const int rc_pp = fe_gram_PtP(P, G_PP, Pm->side);
+    if (rc_pp == FE_OK)
+        FE_TRY_CUDA(cudaMemcpyAsync(G_PP_host, G_PP, gb, cudaMemcpyDeviceToHost, Pm->side), "fe_apply_H_gram_host: copy G_PP out");
+    FE_TRY_CUDA(cudaEventRecord(Pm->ev_join, Pm->side), "fe_apply_H_gram_host: join");
+    rc = fe_apply_H(m, P, Y, stream);
+    if (rc == FE_OK) {
+        FE_TRY_CUDA(cudaEventRecord(Pm->ev_y, s), "fe_apply_H_gram_host: Y ready");
+        FE_TRY_CUDA(cudaStreamWaitEvent(Pm->copy, Pm->ev_y, 0), "fe_apply_H_gram_host: Y ready");
+        FE_TRY_CUDA(cudaMemcpyAsync(Y_host, Y->values, vb, cudaMemcpyDeviceToHost, Pm->copy), "fe_apply_H_gram_host: copy Y out");
+        FE_TRY_CUDA(cudaEventRecord(Pm->ev_copied, Pm->copy), "fe_apply_H_gram_host: Y copied");
+        rc = fe_gram_PtY(P, Y, G_PY, stream);
+        if (rc == FE_OK)
+            FE_TRY_CUDA(cudaMemcpyAsync(G_PY_host, G_PY, gb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy G_PY out");
+        FE_TRY_CUDA(cudaStreamWaitEvent(s, Pm->ev_copied, 0), "fe_apply_H_gram_host: join copy");
+    }
+    FE_TRY_CUDA(cudaStreamWaitEvent(s, Pm->ev_join, 0), "fe_apply_H_gram_host: join");
     FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_apply_H_gram_host: synchronize");
-    return FE_OK;
+    return rc != FE_OK ? rc : rc_pp;
 }
 
 int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream) {
@@ -1323,7 +1364,8 @@ int mmult_impl(const fe_bcsr* A, const double* X, double alpha, double gamma, do
     a.gamma = gamma;
     a.beta = beta;
     a.status = A->mesh ? A->mesh->status : nullptr;
-    FE_TRY_CUDA(launch_mmult<T>(a, s), "fe_mmult: kernel launch");
+    float* x_round = reinterpret_cast<float*>(static_cast<char*>(C->tables) + C->off_xround);
+    FE_TRY_CUDA(launch_mmult<T>(a, x_round, s), "fe_mmult: kernel launch");
     return FE_OK;
 }
 
@@ -1355,7 +1397,8 @@ int fe_mmult(const fe_bcsr* A, const double* X, double alpha, double gamma, doub
     if (rc) return rc;
     if (!X && A->n_values > 0) return fail(FE_EINVAL, "fe_mmult: X is NULL");
     if (A == C) return fail(FE_EINVAL, "fe_mmult: C may not alias A");
-    if ((size_t)C->wmax_union * 16 > 96 * 1024) return fail(FE_EUNSUPPORTED, "fe_mmult: a row block holds %d columns", C->wmax_union);
+    if (C->wmax_union > 6144)
+        return fail(FE_EUNSUPPORTED, "fe_mmult: a row block's stored blocks hold %d (padded) columns; at most 6144", C->wmax_union);
     cudaStream_t s = (cudaStream_t)stream;
     return A->dtype == FE_F64 ? mmult_impl<double>(A, X, alpha, gamma, beta, C, s)
                               : mmult_impl<float>(A, X, alpha, gamma, beta, C, s);

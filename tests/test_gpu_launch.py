@@ -90,3 +90,48 @@ def test_autotune_and_cache(tmp_path):
     torch.cuda.synchronize()
     r = O.run(pb.cfg, fp32_inputs=True)
     assert _relerr(d["G_PY"].cpu().numpy(), r.G_PY[np.ix_(pb.perm, pb.perm)]) <= TOL[1]["PY"]
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+@pytest.mark.parametrize("dtype", [2, 1], ids=["f64", "f32"])
+def test_host_buffer_entry_matches_device_step(dtype, pinned):
+    """fe_apply_H_gram_host (copies in and out around the step, Y and G_PP
+    leaving on their own streams) returns what the device step computes, and
+    the oracle's result; two calls in a row with new P values follow them."""
+    import torch
+    from paper_1907_01005_gb300 import apply_H_gram, apply_H_gram_host
+    cfg = inputs.get_config("small_p2")
+    pb = _setup("small_p2", dtype)
+    d = pb.dev
+    M = pb.n_cols
+    tdt = d["P"].dtype
+
+    def host(t):
+        return t.pin_memory() if pinned else t
+    Ph = host(torch.from_numpy(pb.P_host.copy()))
+    Yh = host(torch.zeros(d["Y"].shape, dtype=tdt))
+    G1 = host(torch.zeros((M, M), dtype=torch.float64))
+    G2 = host(torch.zeros((M, M), dtype=torch.float64))
+    apply_H_gram_host(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], Ph, Yh, G1, G2)
+    assert pb.mesh.check_device() == 0
+    r = O.run(cfg, fp32_inputs=(dtype == 1))
+    from paper_1907_01005_gb300 import harness
+    dofs, cols, vals = harness.unpack_entries(pb, Yh.numpy())
+    ref = np.asarray(r.Y.tocsr()[pb.keys[dofs], pb.perm[cols]]).ravel()
+    assert _relerr(vals, ref) <= TOL[dtype]["Y"]
+    assert _relerr(G1.numpy(), r.G_PY[np.ix_(pb.perm, pb.perm)]) <= TOL[dtype]["PY"]
+    assert _relerr(G2.numpy(), r.G_PP[np.ix_(pb.perm, pb.perm)]) <= TOL[dtype]["PP"]
+    # a second call with P scaled by 2: every output follows (Y by 2, the Grams
+    # by 4), up to the order of the atomic additions into Y (FP32: ~1e-7 of Y,
+    # which P^T Y inherits) and into the Gram matrices
+    Y1, Gpy1, Gpp1 = Yh.numpy().copy(), G1.numpy().copy(), G2.numpy().copy()
+    Ph.mul_(2)
+    apply_H_gram_host(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], Ph, Yh, G1, G2)
+    assert _relerr(Yh.numpy(), 2 * Y1) <= 1e-6
+    assert _relerr(G1.numpy(), 4 * Gpy1) <= (1e-12 if dtype == 2 else TOL[1]["PY"])
+    assert _relerr(G2.numpy(), 4 * Gpp1) <= 1e-12
+    # the device step on the same (scaled) P agrees
+    apply_H_gram(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"])
+    torch.cuda.synchronize()
+    assert _relerr(d["Y"].cpu().numpy(), Yh.numpy()) <= 1e-6
+    assert _relerr(d["G_PP"].cpu().numpy(), G2.numpy()) <= 1e-14

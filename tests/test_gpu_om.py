@@ -104,3 +104,64 @@ def test_om_gradient_and_trace(name, dtype):
     Dsp = _to_sparse(pb, D.values.cpu().numpy())
     gref = O.trace_dot(Dsp, Gref)
     assert abs(float(g.item()) - gref) <= tol * O.trace_dot(abs(Dsp), abs(Gref))
+
+
+def _rows_sparse(pb, values, rbs):
+    """The stored entries of row blocks `rbs` as a sparse (n_nodes, M) matrix
+    in oracle coordinates (lattice keys, orbital ids)."""
+    offs, ld = pb.P.block_offsets(), pb.P.row_strides()
+    dofs, cols, vals = [], [], []
+    for r in rbs:
+        nr = int(pb.rb_ptr[r + 1] - pb.rb_ptr[r])
+        for k in range(pb.row_ptr[r], pb.row_ptr[r + 1]):
+            c = pb.col_idx[k]
+            w = int(pb.cbp[c + 1] - pb.cbp[c])
+            vals.append(values[offs[k]: offs[k] + nr * ld[c]].reshape(nr, ld[c])[:, :w].ravel())
+            dofs.append(np.repeat(np.arange(pb.rb_ptr[r], pb.rb_ptr[r + 1]), w))
+            cols.append(np.tile(np.arange(pb.cbp[c], pb.cbp[c + 1]), nr))
+    dofs, cols, vals = np.concatenate(dofs), np.concatenate(cols), np.concatenate(vals).astype(np.float64)
+    n = int(pb.mesh.info.lx * pb.mesh.info.ly * pb.mesh.info.lz)
+    return sp.csc_matrix((vals, (pb.keys[dofs], pb.perm[cols])), shape=(n, pb.n_cols))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype", [2, 1], ids=["f64", "f32"])
+def test_mmult_paper_scale_sampled(dtype):
+    """846,369 DoFs x 320 orbitals at p = 2: row blocks hold up to 17 column
+    blocks, so the widest span several 128-column chunks and the boundary
+    ones several 64-row chunks.  Checked on the widest row blocks, boundary
+    row blocks and random ones against the oracle's Alg. 7 on those rows."""
+    import torch
+    from paper_1907_01005_gb300 import harness, mmult
+    cfg = inputs.get_config("p2")
+    pb = harness.build_problem(cfg, dtype)
+    harness.to_device(pb)
+    M = pb.n_cols
+    X = np.random.default_rng(5).normal(size=(M, M))
+    C = _like(pb)
+    C.values.normal_()
+    C0 = C.values.cpu().numpy().copy()
+    mmult(pb.P, torch.from_numpy(X).cuda(), C, alpha=0.5, gamma=-1.5, beta=2.0)
+    torch.cuda.synchronize()
+    assert pb.mesh.check_device() == 0
+    Cv = C.values.cpu().numpy()
+    nblk = np.diff(pb.row_ptr)
+    rows = np.diff(pb.rb_ptr)
+    rng = np.random.default_rng(6)
+    rbs = np.unique(np.concatenate([np.argsort(nblk)[-8:], np.nonzero(rows > 64)[0][:6],
+                                    rng.choice(np.nonzero(nblk > 0)[0], 12, replace=False)]))
+    mesh = O.BoxMesh.from_config(cfg)
+    blk = O.Blocking(mesh)
+    centres = inputs.orbital_centres(cfg)
+    perm, ptr = O.column_blocks(blk, centres, cfg.n_col_blocks)
+    mv = O.build_orbitals(mesh, cfg, centres, round_fp32=(dtype == 1))
+    pat = O.block_pattern(blk, mv, perm, ptr)
+    cb_of_orb = O.entry_mask(blk, pat, perm, ptr)
+    Xo = np.empty_like(X)
+    Xo[np.ix_(pb.perm, pb.perm)] = X
+    A = _rows_sparse(pb, pb.P_host, rbs)
+    ref = 0.5 * (O.mmult_masked(A, Xo, blk, pat, cb_of_orb) - 1.5 * A) + 2.0 * _rows_sparse(pb, C0, rbs)
+    got = _rows_sparse(pb, Cv, rbs)
+    tol = 1e-12 if dtype == 2 else 1e-5
+    err = abs(got - ref).max() / abs(ref).max()            # sparse: the dense matrix would be 2 GB
+    assert err <= tol, err
