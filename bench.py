@@ -228,14 +228,17 @@ def load_bf16_peak():
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the FP32 p2 workload, with the SHA-256 of the kernel's source
-# file at capture time; reported only while that source is unchanged.
-_SHA_GRAM = "5d7d3e1570deae93ac6c6596adee28817d6d881d9c74b9a11eeadea462989a77"
-_SHA_APPLY = "0659cfe6e8aa43ae4a79cdca27e2c8e579eddc3bbf434c07a2224d600f9d97dd"
+# ncu capture of the FP32 p2 workload (profiles/*_p2_f32.md), with the SHA-256
+# of the kernel's source files at capture time; reported only while those
+# sources are unchanged.
+_SRC_GRAM = ("gram_tc.cu",)
+_SRC_APPLY = ("apply_unit.cu", "unit_common.cuh")
+_SRC_MMULT = ("mmult.cu",)
 NCU_TRAFFIC = {
-    "gram_py": ("gram_tc.cu", _SHA_GRAM, 507036928),
-    "gram_pp": ("gram_tc.cu", _SHA_GRAM, 256380928),
-    "apply": ("apply_unit.cu", _SHA_APPLY, 670181120),
+    "gram_py": (_SRC_GRAM, "2f73977a3ff2127e2a1418246419ed76d1a583468eaad8f4b343ff72c8ecb8ef", 508275968),
+    "gram_pp": (_SRC_GRAM, "2f73977a3ff2127e2a1418246419ed76d1a583468eaad8f4b343ff72c8ecb8ef", 256380928),
+    "apply": (_SRC_APPLY, "c1fb8ab74a49dd1a08d39fd263686c0bf29db0af8f0ce8c1dd93bdfa34a88357", 669903360),
+    "mmult": (_SRC_MMULT, "1ba37459ab68dc9c047f3d4afc08675456773d90c7df21aa698aea12cea384b5", 706672384),
 }
 
 
@@ -243,11 +246,11 @@ def ncu_traffic(kernel, config_name):
     import hashlib
     if config_name != "p2" or kernel not in NCU_TRAFFIC:
         return None
-    fname, sha, nbytes = NCU_TRAFFIC[kernel]
-    path = os.path.join(ROOT, "paper_1907_01005_gb300", "csrc", fname)
-    if hashlib.sha256(open(path, "rb").read()).hexdigest() != sha:
-        return None
-    return nbytes
+    files, sha, nbytes = NCU_TRAFFIC[kernel]
+    h = hashlib.sha256()
+    for fname in files:
+        h.update(open(os.path.join(ROOT, "paper_1907_01005_gb300", "csrc", fname), "rb").read())
+    return nbytes if h.hexdigest() == sha else None
 
 
 def probe_alu(dtype):
@@ -543,9 +546,12 @@ def main():
     # the rest of an orbital-minimisation gradient evaluation (NEXT rows f1, f3)
     om = time_om(pb, max(10, args.steps // 10))
     t_mm = om["mmult_1"] * 1e-3
+    t_mm2 = om["mmult_2"] * 1e-3
     om["mmult_roofline"] = {"bound": "alu", "achieved": info.gram_flops / t_mm / 1e12, "peak": fp32_peak / 1e12,
                             "unit": "TFLOP/s", "frac": info.gram_flops / t_mm / fp32_peak,
-                            "hbm_frac": 2 * nnz * s / t_mm / 1e9 / hbm_peak}
+                            "hbm_frac": 2 * nnz * s / t_mm / 1e9 / hbm_peak,
+                            "traffic_beta1": ncu_traffic("mmult", cfg.name),
+                            "hbm_frac_beta1": 3 * nnz * s / t_mm2 / 1e9 / hbm_peak}
     om["gradient_ms"] = ms_step + om["total_ms"]      # H P, Hbar, P^T P (the step) plus the above
     line["om"] = om
 
