@@ -29,7 +29,6 @@ struct UnitGeo {
     static constexpr int L = kUnitLanes;             // columns of a unit, one per thread of a cell
     static constexpr int THREADS = 8 * L;
     static constexpr int CH = 16 / sizeof(T);          // elements per 16-byte chunk
-    static constexpr int MAXCH = kUnitLdSum / CH;      // chunks per node row of the unit
     static constexpr int TEN = NPN * kUnitLdSum;       // elements of one patch tensor (all blocks)
     // gathered input U, accumulated output Yp, V at the Gauss points
     static constexpr size_t bytes = (size_t)(2 * TEN + 8 * N3) * sizeof(T);
@@ -45,14 +44,14 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     apply_unit_kernel(const ApplyUnitArgs<T> a) {
     using G = UnitGeo<T, P>;
     constexpr int N = G::N, NP = G::NP, NPN = G::NPN, N3 = G::N3, L = G::L;
-    constexpr int CH = G::CH, MAXCH = G::MAXCH;
+    constexpr int CH = G::CH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* U = reinterpret_cast<T*>(smem_raw);         // per block b: [NPN][ld_b] at sBase[b]
     T* Yp = U + G::TEN;                            // same layout, accumulated cell results
     T* Vs = Yp + G::TEN;                           // [8][N3]  V at the Gauss points
     __shared__ int32_t sOff[kUnitBlocks][8];
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks], sW[kUnitBlocks];
-    __shared__ int sChB[MAXCH], sChC[MAXCH], sNch, sTen, sMagic;
+    __shared__ int sTen;
     __shared__ int sNode[NPN];                     // (slot << 16) | row, or -1 on the boundary
     __shared__ int64_t sItem;
     const int tid = threadIdx.x;
@@ -99,37 +98,39 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         sOff[tid >> 3][tid & 7] = (tid >> 3) < unit.nb ? unit.off[tid >> 3][tid & 7] : -1;
     }
     if (tid == 0) {
-        int base = 0, nch = 0;
+        int base = 0;
         for (int q = 0; q < kUnitBlocks; ++q) {
             const int ldq = q < unit.nb ? unit.ld[q] : 0;
             sBase[q] = base;
             sLd[q] = ldq;
             sW[q] = q < unit.nb ? unit.width[q] : 0;
             sMask[q] = q < unit.nb ? unit.cellmask[q] : 0;
-            for (int c0 = 0; c0 < ldq; c0 += CH) { sChB[nch] = q; sChC[nch] = c0; ++nch; }
             base += NPN * ldq;
         }
-        sNch = nch;
         sTen = base;
-        sMagic = (65536 + nch - 1) / nch;         // e / nch == (e * sMagic) >> 16 for e < NPN * nch
     }
     for (int n = tid; n < NPN; n += blockDim.x) sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
     __syncthreads();
 
-    const int nch = sNch, magic = sMagic, ntask = NPN * nch;
-    // ---- gather: asynchronous 16-byte copies of block row chunks ------------
+    static_assert(kUnitBlocks == 4, "task index: node << 2 | block");
+    const int nb = unit.nb;
+    // ---- gather: asynchronous 16-byte copies of block rows ------------------
+    // one task per (node, block): the row's table lookups once, then its
+    // 16-byte chunks
     {
         const unsigned ubase = (unsigned)__cvta_generic_to_shared(U);
-        for (int e = tid; e < ntask; e += blockDim.x) {
-            const int node = (e * magic) >> 16, j = e - node * nch;
-            const int b = sChB[j], c0 = sChC[j], ld = sLd[b];
+        for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
+            const int node = e >> 2, b = e & 3;
+            if (b >= nb) continue;
+            const int ld = sLd[b];
             const int ne = sNode[node];
             const int32_t o = ne >= 0 ? sOff[b][ne >> 16] : -1;
             const bool ok = o >= 0;
-            const T* src = ok ? a.P + (int64_t)o * kElem16 + (ne & 0xffff) * ld + c0 : a.P;
-            const unsigned dst = ubase + (unsigned)((sBase[b] + node * ld + c0) * sizeof(T));
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
-                         "r"(ok ? 16 : 0) : "memory");
+            const T* src = ok ? a.P + (int64_t)o * kElem16 + (ne & 0xffff) * ld : a.P;
+            const unsigned dst = ubase + (unsigned)((sBase[b] + node * ld) * sizeof(T));
+            for (int c0 = 0; c0 < ld; c0 += CH)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + c0 * (int)sizeof(T)),
+                             "l"(ok ? src + c0 : src), "r"(ok ? 16 : 0) : "memory");
         }
         // the potential of the patch's cells (contiguous, 16-byte aligned)
         if constexpr (!MASS) {
@@ -223,26 +224,30 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     __syncthreads();
 
     // ---- scatter-add of 16-byte chunks (Alg. 6, write step) -----------------
-    for (int e = tid; e < ntask; e += blockDim.x) {
-        const int node = (e * magic) >> 16, j = e - node * nch;
+    for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
+        const int node = e >> 2, b = e & 3;
+        if (b >= nb) continue;
         const int ne = sNode[node];
         if (ne < 0) continue;
-        const int b = sChB[j];
         const int32_t o = sOff[b][ne >> 16];
         if (o < 0) continue;
-        const int c0 = sChC[j], ld = sLd[b];
-        T v[CH];
-        if constexpr (CH == 4) {
-            const float4 f = *reinterpret_cast<const float4*>(Yp + sBase[b] + node * ld + c0);
-            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-        } else {
-            const double2 f = *reinterpret_cast<const double2*>(Yp + sBase[b] + node * ld + c0);
-            v[0] = f.x; v[1] = f.y;
-        }
-        bool nz = false;
+        const int ld = sLd[b];
+        const T* ys = Yp + sBase[b] + node * ld;
+        T* yd = a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld;
+        for (int c0 = 0; c0 < ld; c0 += CH) {
+            T v[CH];
+            if constexpr (CH == 4) {
+                const float4 f = *reinterpret_cast<const float4*>(ys + c0);
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+            } else {
+                const double2 f = *reinterpret_cast<const double2*>(ys + c0);
+                v[0] = f.x; v[1] = f.y;
+            }
+            bool nz = false;
 #pragma unroll
-        for (int q = 0; q < CH; ++q) nz |= v[q] != T(0);
-        if (nz) red_chunk(a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld + c0, v);
+            for (int q = 0; q < CH; ++q) nz |= v[q] != T(0);
+            if (nz) red_chunk(yd + c0, v);
+        }
     }
     }  // unit_ok
     if (!a.ticket) break;

@@ -108,6 +108,13 @@ CONFIGS: dict[str, Config] = {
     "narrow_p4": _cfg(name="narrow_p4", nx=4, ny=4, nz=6, hx=2.0, hy=2.0, hz=2.0, p=4,
                       n_orb=5, n_col_blocks=5, radius=3.0, env_s2=(3.0 / 1.75) ** 2,
                       n_wells=4, well_depth=1.0, well_sigma=1.0, index=12),
+    # Natural (free) boundary: boundary nodes carry DoFs like interior ones.
+    "free_p2": _cfg(name="free_p2", nx=8, ny=6, nz=4, hx=1.0, hy=1.0, hz=1.0, p=2,
+                    n_orb=29, n_col_blocks=4, radius=1.8, env_s2=(1.8 / 1.75) ** 2,
+                    n_wells=4, well_depth=1.0, well_sigma=1.0, dirichlet=0, index=13),
+    "free_p4": _cfg(name="free_p4", nx=4, ny=4, nz=2, hx=2.0, hy=2.0, hz=2.0, p=4,
+                    n_orb=21, n_col_blocks=3, radius=3.0, env_s2=(3.0 / 1.75) ** 2,
+                    n_wells=4, well_depth=1.0, well_sigma=1.0, dirichlet=0, index=14),
     # Paper scale, p=2: 64x40x40 unit Q2 cells = 102,400 cells, 846,369 DoFs,
     # 12,800 row blocks; 320 orbitals in 38 column blocks; ~20% block fill;
     # 50 wells of depth 1 and width 2 cells.

@@ -54,7 +54,8 @@ def _problem(name):
     return cfg, harness.build_problem(cfg)
 
 
-@pytest.mark.parametrize("name", ["tiny", "small_p2", "small_p4", "small_p1", "small_p3", "narrow_p4"])
+@pytest.mark.parametrize("name", ["tiny", "small_p2", "small_p4", "small_p1", "small_p3", "narrow_p4", "free_p2",
+                                  "free_p4"])
 def test_host_setup_matches_oracle(lib, name):
     cfg, pb = _problem(name)
     mesh = O.BoxMesh.from_config(cfg)

@@ -12,7 +12,7 @@ from synth import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = dict(Y=1e-5, PY=1e-6, PP=1e-10)
-SMALL = ["tiny", "small_p1", "small_p2", "wide_p2", "narrow_p2"]
+SMALL = ["tiny", "small_p1", "small_p2", "wide_p2", "narrow_p2", "free_p2"]
 
 
 def _relerr(got, ref):

@@ -10,7 +10,7 @@ from synth import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {2: dict(Y=1e-12, PY=1e-12), 1: dict(Y=1e-5, PY=1e-6)}
-NAMES = ["tiny", "tiny_p4", "small_p1", "small_p2", "small_p3", "small_p4", "narrow_p4"]
+NAMES = ["tiny", "tiny_p4", "small_p1", "small_p2", "small_p3", "small_p4", "narrow_p4", "free_p2", "free_p4"]
 
 
 def _relerr(got, ref):
