@@ -105,18 +105,19 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
     }
     __syncthreads();
     constexpr int CH = 16 / sizeof(T);               // elements per 16-byte chunk (ld is a multiple)
-    const int nch = ld / CH, ntask = NPN * nch;
 
-    // ---- gather (Alg. 6, read step): 16-byte asynchronous copies -------------
+    // ---- gather (Alg. 6, read step): 16-byte asynchronous copies, one task
+    // per node row (the node table is read once, then the row's chunks) ------
     {
         const unsigned ubase = (unsigned)__cvta_generic_to_shared(U);
-        for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
-            const int node = e / nch, q = e - node * nch;
+        for (int node = threadIdx.x; node < NPN; node += blockDim.x) {
             const int ne = sNode[node];
             const bool ok = ne >= 0;
-            const T* src = ok ? a.P + sOff[ne >> 16] + (int64_t)(ne & 0xffff) * ld + q * CH : a.P;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(ubase + (unsigned)((node * ld + q * CH) * sizeof(T))),
-                         "l"(src), "r"(ok ? 16 : 0) : "memory");
+            const T* src = ok ? a.P + sOff[ne >> 16] + (int64_t)(ne & 0xffff) * ld : a.P;
+            const unsigned dst = ubase + (unsigned)(node * ld * sizeof(T));
+            for (int c0 = 0; c0 < ld; c0 += CH)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + c0 * (int)sizeof(T)),
+                             "l"(ok ? src + c0 : src), "r"(ok ? 16 : 0) : "memory");
         }
         for (int e = threadIdx.x; e < NPN * ld / CH; e += blockDim.x)
             reinterpret_cast<uint4*>(Yp)[e] = make_uint4(0u, 0u, 0u, 0u);
@@ -285,19 +286,27 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
         __syncthreads();
     }
 
-    // ---- scatter-add (Alg. 6, write step): 16-byte vector reductions ----------
-    for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
-        const int node = e / nch, q = e - node * nch;
+    // ---- scatter-add (Alg. 6, write step): 16-byte vector reductions, one
+    // task per node row ---------------------------------------------------------
+    for (int node = threadIdx.x; node < NPN; node += blockDim.x) {
         const int ne = sNode[node];
         if (ne < 0) continue;
-        T v[CH];
-        bool nz = false;
+        const T* ys = Yp + node * ld;
+        T* yd = a.Y + sOff[ne >> 16] + (int64_t)(ne & 0xffff) * ld;
+        for (int c0 = 0; c0 < ld; c0 += CH) {
+            T v[CH];
+            if constexpr (CH == 4) {
+                const float4 f = *reinterpret_cast<const float4*>(ys + c0);
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+            } else {
+                const double2 f = *reinterpret_cast<const double2*>(ys + c0);
+                v[0] = f.x; v[1] = f.y;
+            }
+            bool nz = false;
 #pragma unroll
-        for (int h = 0; h < CH; ++h) {
-            v[h] = Yp[node * ld + q * CH + h];          // padding columns stay zero
-            nz |= v[h] != T(0);
+            for (int h = 0; h < CH; ++h) nz |= v[h] != T(0);   // padding columns stay zero
+            if (nz) red_chunk(yd + c0, v);
         }
-        if (nz) red_chunk(a.Y + sOff[ne >> 16] + (int64_t)(ne & 0xffff) * ld + q * CH, v);
     }
 }
 

@@ -44,7 +44,6 @@ struct CmGeo {
     static constexpr int L = kUnitLanes;
     static constexpr int THREADS = 8 * L;          // one A row per thread: 2 tiles of 128
     static constexpr int CH = 4;                   // floats per 16-byte chunk
-    static constexpr int MAXCH = kUnitLdSum / CH;
     static constexpr int TEN = NPN * kUnitLdSum;   // floats of the patch tensor
     static constexpr int TILE = 128 * 128;         // bytes of a 128-row operand tile (rows of 32 floats)
     // dynamic shared memory, from a 1024-byte aligned base (the period of the
@@ -196,14 +195,14 @@ template <int P, bool MASS>
 __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(const CellMatArgs a) {
     using G = CmGeo<P>;
     constexpr int N = G::N, NP = G::NP, NPN = G::NPN, N3 = G::N3, L = G::L, NPAD = G::NPAD;
-    constexpr int CH = G::CH, MAXCH = G::MAXCH, KSTEPS = G::KSTEPS, KCH = (8 * KSTEPS) / 4;
+    constexpr int CH = G::CH, KSTEPS = G::KSTEPS, KCH = (8 * KSTEPS) / 4;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     unsigned char* sm = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
     float* U = reinterpret_cast<float*>(sm + G::OFF_U);    // gathered patch tensor, then the cells' results
     float* Vs = reinterpret_cast<float*>(sm + G::OFF_V);   // [8][N3]
     __shared__ int32_t sOff[kUnitBlocks][8];
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
-    __shared__ int sChB[MAXCH], sChC[MAXCH], sNch, sTen, sMagic;
+    __shared__ int sTen;
     __shared__ int sNode[NPN];
     __shared__ int64_t sItem;
     __shared__ __align__(8) uint64_t sBar;
@@ -279,36 +278,36 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                 sOff[tid >> 3][tid & 7] = (tid >> 3) < unit.nb ? unit.off[tid >> 3][tid & 7] : -1;
             }
             if (tid == 0) {
-                int base = 0, nch = 0;
+                int base = 0;
                 for (int q = 0; q < kUnitBlocks; ++q) {
                     const int ldq = q < unit.nb ? unit.ld[q] : 0;
                     sBase[q] = base;
                     sLd[q] = ldq;
                     sMask[q] = q < unit.nb ? unit.cellmask[q] : 0;
-                    for (int c0 = 0; c0 < ldq; c0 += CH) { sChB[nch] = q; sChC[nch] = c0; ++nch; }
                     base += NPN * ldq;
                 }
-                sNch = nch;
                 sTen = base;
-                sMagic = (65536 + nch - 1) / nch;     // e / nch == (e * sMagic) >> 16 for e < NPN * nch
             }
             for (int n = tid; n < NPN; n += blockDim.x) sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
             __syncthreads();
 
-            const int nch = sNch, magic = sMagic, ntask = NPN * nch;
-            // ---- gather -----------------------------------------------------
+            static_assert(kUnitBlocks == 4, "task index: node << 2 | block");
+            const int nb = unit.nb;
+            // ---- gather: one task per (node, block) row ----------------------
             {
                 const unsigned ubase = smem_u32(U);
-                for (int e = tid; e < ntask; e += blockDim.x) {
-                    const int node = (e * magic) >> 16, j = e - node * nch;
-                    const int b = sChB[j], c0 = sChC[j], ld = sLd[b];
+                for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
+                    const int node = e >> 2, b = e & 3;
+                    if (b >= nb) continue;
+                    const int ld = sLd[b];
                     const int ne = sNode[node];
                     const int32_t o = ne >= 0 ? sOff[b][ne >> 16] : -1;
                     const bool ok = o >= 0;
-                    const float* src = ok ? a.P + (int64_t)o * 4 + (ne & 0xffff) * ld + c0 : a.P;
-                    const unsigned dst = ubase + (unsigned)((sBase[b] + node * ld + c0) * 4);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
-                                 "r"(ok ? 16 : 0) : "memory");
+                    const float* src = ok ? a.P + (int64_t)o * 4 + (ne & 0xffff) * ld : a.P;
+                    const unsigned dst = ubase + (unsigned)((sBase[b] + node * ld) * 4);
+                    for (int c0 = 0; c0 < ld; c0 += CH)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + 4 * c0),
+                                     "l"(ok ? src + c0 : src), "r"(ok ? 16 : 0) : "memory");
                 }
                 if constexpr (!MASS) {
                     const float* Vg = a.Vq + (int64_t)unit.patch * 8 * N3;
@@ -422,19 +421,22 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
             tc_fence_before();
             __syncthreads();
 
-            // ---- scatter-add of 16-byte chunks --------------------------------
-            for (int e = tid; e < ntask; e += blockDim.x) {
-                const int node = (e * magic) >> 16, j = e - node * nch;
+            // ---- scatter-add of 16-byte chunks, one task per (node, block) row -
+            for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
+                const int node = e >> 2, bb = e & 3;
+                if (bb >= nb) continue;
                 const int ne = sNode[node];
                 if (ne < 0) continue;
-                const int bb = sChB[j];
                 const int32_t o = sOff[bb][ne >> 16];
                 if (o < 0) continue;
-                const int c0 = sChC[j], ldb = sLd[bb];
-                const float4 f = *reinterpret_cast<const float4*>(U + sBase[bb] + node * ldb + c0);
-                const float v[4] = {f.x, f.y, f.z, f.w};
-                if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f)
-                    red_chunk(a.Y + (int64_t)o * 4 + (ne & 0xffff) * ldb + c0, v);
+                const int ldb = sLd[bb];
+                const float* ys = U + sBase[bb] + node * ldb;
+                float* yd = a.Y + (int64_t)o * 4 + (ne & 0xffff) * ldb;
+                for (int c0 = 0; c0 < ldb; c0 += CH) {
+                    const float4 f = *reinterpret_cast<const float4*>(ys + c0);
+                    const float v[4] = {f.x, f.y, f.z, f.w};
+                    if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f) red_chunk(yd + c0, v);
+                }
             }
         }  // unit_ok
         __syncthreads();                                  // shared tables are rebuilt for the next unit
