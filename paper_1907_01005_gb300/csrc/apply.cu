@@ -16,6 +16,7 @@
 #include <cstdio>
 
 #include "fe_internal.h"
+#include "unit_common.cuh"
 
 namespace femf {
 namespace {
@@ -49,16 +50,6 @@ __device__ __forceinline__ void node_slot_row(int i, int j, int k, int px, int p
 
 __device__ __forceinline__ bool on_boundary(int I, int J, int K, int lx, int ly, int lz) {
     return I == 0 || J == 0 || K == 0 || I == lx - 1 || J == ly - 1 || K == lz - 1;
-}
-
-// 16-byte chunk of one block row added into Y
-__device__ __forceinline__ void red_chunk(float* dst, const float* v) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(dst), "f"(v[0]), "f"(v[1]), "f"(v[2]),
-                 "f"(v[3]) : "memory");
-}
-__device__ __forceinline__ void red_chunk(double* dst, const double* v) {
-    if (v[0] != 0.0) atomicAdd(dst, v[0]);
-    if (v[1] != 0.0) atomicAdd(dst + 1, v[1]);
 }
 
 __device__ __forceinline__ void atomic_add_shared(float* a, float v) { atomicAdd(a, v); }

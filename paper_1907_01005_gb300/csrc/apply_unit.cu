@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     T* Yp = U + G::TEN;                            // same layout, accumulated cell results
     T* Vs = Yp + G::TEN;                           // [8][N3]  V at the Gauss points
     __shared__ int32_t sOff[kUnitBlocks][8];
-    __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks], sW[kUnitBlocks];
+    __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
     __shared__ int sTen;
     __shared__ int sNode[NPN];                     // (slot << 16) | row, or -1 on the boundary
     __shared__ int64_t sItem;
@@ -103,7 +103,6 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
             const int ldq = q < unit.nb ? unit.ld[q] : 0;
             sBase[q] = base;
             sLd[q] = ldq;
-            sW[q] = q < unit.nb ? unit.width[q] : 0;
             sMask[q] = q < unit.nb ? unit.cellmask[q] : 0;
             base += NPN * ldq;
         }

@@ -1,7 +1,7 @@
-// Device helpers shared by the two kernels that process packed work units
-// (apply_unit.cu: sum factorisation in registers; apply_cellmat.cu: cell
-// matrices on the tensor cores): the patch-node table and the 16-byte
-// scatter-add into Y.
+// Device helpers shared by the apply kernels (apply_unit.cu: sum
+// factorisation in registers; apply_cellmat.cu: cell matrices on the tensor
+// cores; apply.cu: the p >= 3 plane kernel): the patch-node table of the
+// packed-unit kernels and the 16-byte scatter-add into Y.
 #pragma once
 
 #include "fe_internal.h"
