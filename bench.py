@@ -237,7 +237,7 @@ _SRC_MMULT = ("mmult.cu",)
 NCU_TRAFFIC = {
     "gram_py": (_SRC_GRAM, "2f73977a3ff2127e2a1418246419ed76d1a583468eaad8f4b343ff72c8ecb8ef", 508275968),
     "gram_pp": (_SRC_GRAM, "2f73977a3ff2127e2a1418246419ed76d1a583468eaad8f4b343ff72c8ecb8ef", 256380928),
-    "apply": (_SRC_APPLY, "c1fb8ab74a49dd1a08d39fd263686c0bf29db0af8f0ce8c1dd93bdfa34a88357", 669903360),
+    "apply": (_SRC_APPLY, "97d1b663b1c66bfbb458480b05dfe46bfc2da0190b77dd07c0ef70819fff92b4", 665428736),
     "mmult": (_SRC_MMULT, "1ba37459ab68dc9c047f3d4afc08675456773d90c7df21aa698aea12cea384b5", 706672384),
 }
 
