@@ -10,9 +10,12 @@
 //
 // Data movement works on 16-byte row chunks (block rows are padded to 16
 // bytes): the gather is a set of asynchronous 16-byte copies (cp.async, zero
-// fill for absent blocks and boundary nodes) into a per-block patch tensor
-// U_b[node][ld_b]; the cells add their results into a matching zeroed
-// tensor with shared-memory atomics; the scatter adds 16-byte chunks into Y
+// fill for absent blocks and boundary nodes) into a patch tensor
+// U[node][kUnitLdSum] whose rows hold the unit's blocks side by side (the 32
+// lanes of a warp then read one row: no bank conflicts between blocks, and
+// the row stride is a compile-time constant); the
+// cells add their results into a matching zeroed tensor with shared-memory
+// atomics; the scatter adds 16-byte chunks into Y
 // with vector reductions (red.global.add.v4.f32), 4x fewer than scalar
 // atomics.
 #include <algorithm>
@@ -46,12 +49,11 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     constexpr int N = G::N, NP = G::NP, NPN = G::NPN, N3 = G::N3, L = G::L;
     constexpr int CH = G::CH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* U = reinterpret_cast<T*>(smem_raw);         // per block b: [NPN][ld_b] at sBase[b]
+    T* U = reinterpret_cast<T*>(smem_raw);         // [NPN][kUnitLdSum]: block b at columns sBase[b] ..
     T* Yp = U + G::TEN;                            // same layout, accumulated cell results
     T* Vs = Yp + G::TEN;                           // [8][N3]  V at the Gauss points
     __shared__ int32_t sOff[kUnitBlocks][8];
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
-    __shared__ int sTen;
     __shared__ int sNode[NPN];                     // (slot << 16) | row, or -1 on the boundary
     __shared__ int64_t sItem;
     const int tid = threadIdx.x;
@@ -101,18 +103,18 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         int base = 0;
         for (int q = 0; q < kUnitBlocks; ++q) {
             const int ldq = q < unit.nb ? unit.ld[q] : 0;
-            sBase[q] = base;
+            sBase[q] = base;                       // first column of block q in a node row
             sLd[q] = ldq;
             sMask[q] = q < unit.nb ? unit.cellmask[q] : 0;
-            base += NPN * ldq;
+            base += ldq;
         }
-        sTen = base;
     }
     for (int n = tid; n < NPN; n += blockDim.x) sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
     __syncthreads();
 
     static_assert(kUnitBlocks == 4, "task index: node << 2 | block");
     const int nb = unit.nb;
+    constexpr int S = kUnitLdSum;                  // node row: the unit's blocks side by side
     // ---- gather: asynchronous 16-byte copies of block rows ------------------
     // one task per (node, block): the row's table lookups once, then its
     // 16-byte chunks
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
             const int32_t o = ne >= 0 ? sOff[b][ne >> 16] : -1;
             const bool ok = o >= 0;
             const T* src = ok ? a.P + (int64_t)o * kElem16 + (ne & 0xffff) * ld : a.P;
-            const unsigned dst = ubase + (unsigned)((sBase[b] + node * ld) * sizeof(T));
+            const unsigned dst = ubase + (unsigned)((node * S + sBase[b]) * sizeof(T));
             for (int c0 = 0; c0 < ld; c0 += CH)
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + c0 * (int)sizeof(T)),
                              "l"(ok ? src + c0 : src), "r"(ok ? 16 : 0) : "memory");
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
                              : "memory");
         }
         // zero the output tensor while the copies are in flight
-        const int ten4 = sTen / CH;
+        const int ten4 = NPN * S / CH;
         for (int e = tid; e < ten4; e += blockDim.x) reinterpret_cast<uint4*>(Yp)[e] = make_uint4(0u, 0u, 0u, 0u);
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
@@ -153,16 +155,15 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         const int b = sLaneB[lane];
         const bool act = b >= 0 && ((sMask[b] >> cell) & 1);
         if (act) {
-            const int ld = sLd[b];
             // element of local node (z, y, x) of this cell in both patch tensors
-            const int base = sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * ld;
+            const int base = sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * S;
             T u[N][N][N], t[N][N][N];
 #pragma unroll
             for (int z = 0; z < N; ++z)
 #pragma unroll
                 for (int y = 0; y < N; ++y)
 #pragma unroll
-                    for (int x = 0; x < N; ++x) u[z][y][x] = U[base + ((z * NP + y) * NP + x) * ld];
+                    for (int x = 0; x < N; ++x) u[z][y][x] = U[base + ((z * NP + y) * NP + x) * S];
             const auto& K = a.k;
             // Sweeps run coefficient-outer: each coefficient is applied to all
             // N^2 lines of the sweep.
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
 #pragma unroll
                 for (int y = 0; y < N; ++y)
 #pragma unroll
-                    for (int x = 0; x < N; ++x) atomicAdd(&Yp[base + ((z * NP + y) * NP + x) * ld], t[z][y][x]);
+                    for (int x = 0; x < N; ++x) atomicAdd(&Yp[base + ((z * NP + y) * NP + x) * S], t[z][y][x]);
         }
     }
     __syncthreads();
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         const int32_t o = sOff[b][ne >> 16];
         if (o < 0) continue;
         const int ld = sLd[b];
-        const T* ys = Yp + sBase[b] + node * ld;
+        const T* ys = Yp + node * S + sBase[b];
         T* yd = a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld;
         for (int c0 = 0; c0 < ld; c0 += CH) {
             T v[CH];
