@@ -23,7 +23,7 @@
 // which leaves an error of about 2^-21 relative per product.
 //
 // Data movement is that of the register kernel: 16-byte cp.async gather of the
-// patch tensor, shared-memory atomics of the cells' results into a zeroed
+// patch tensor (node rows of kUnitLdSum with the unit's blocks side by side), shared-memory atomics of the cells' results into a zeroed
 // patch tensor (here it reuses the gather buffer), 16-byte vector reductions
 // into Y.  The constant operand tiles (both parts of K_L, S3, Sb3) are copied
 // once per CTA; CTAs are persistent and take units from a work counter.
@@ -202,7 +202,6 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
     float* Vs = reinterpret_cast<float*>(sm + G::OFF_V);   // [8][N3]
     __shared__ int32_t sOff[kUnitBlocks][8];
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
-    __shared__ int sTen;
     __shared__ int sNode[NPN];
     __shared__ int64_t sItem;
     __shared__ __align__(8) uint64_t sBar;
@@ -281,18 +280,18 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                 int base = 0;
                 for (int q = 0; q < kUnitBlocks; ++q) {
                     const int ldq = q < unit.nb ? unit.ld[q] : 0;
-                    sBase[q] = base;
+                    sBase[q] = base;                   // first column of block q in a node row
                     sLd[q] = ldq;
                     sMask[q] = q < unit.nb ? unit.cellmask[q] : 0;
-                    base += NPN * ldq;
+                    base += ldq;
                 }
-                sTen = base;
             }
             for (int n = tid; n < NPN; n += blockDim.x) sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
             __syncthreads();
 
             static_assert(kUnitBlocks == 4, "task index: node << 2 | block");
             const int nb = unit.nb;
+            constexpr int S = kUnitLdSum;                 // node row: the unit's blocks side by side
             // ---- gather: one task per (node, block) row ----------------------
             {
                 const unsigned ubase = smem_u32(U);
@@ -304,7 +303,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                     const int32_t o = ne >= 0 ? sOff[b][ne >> 16] : -1;
                     const bool ok = o >= 0;
                     const float* src = ok ? a.P + (int64_t)o * 4 + (ne & 0xffff) * ld : a.P;
-                    const unsigned dst = ubase + (unsigned)((sBase[b] + node * ld) * 4);
+                    const unsigned dst = ubase + (unsigned)((node * S + sBase[b]) * 4);
                     for (int c0 = 0; c0 < ld; c0 += CH)
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + 4 * c0),
                                      "l"(ok ? src + c0 : src), "r"(ok ? 16 : 0) : "memory");
@@ -324,8 +323,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
             // ---- stage 1 operand: the thread's cell-column at its cell's nodes
             const int b = sLaneB[lane];
             const bool act = b >= 0 && ((sMask[b] >> cell) & 1);
-            const int ld = act ? sLd[b] : 0;
-            const int base = act ? sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * ld : 0;
+            const int base = act ? sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * S : 0;
             {
                 float x[4 * KCH];
 #pragma unroll
@@ -337,7 +335,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                         for (int y = 0; y < N; ++y)
 #pragma unroll
                             for (int xx = 0; xx < N; ++xx)
-                                x[(z * N + y) * N + xx] = U[base + ((z * NP + y) * NP + xx) * ld];
+                                x[(z * N + y) * N + xx] = U[base + ((z * NP + y) * NP + xx) * S];
                 }
                 store_row_split<KCH>(aHi, aLo, r, x);
             }
@@ -361,7 +359,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                 mma_commit(bar);
             }
             // zero the patch tensor for the results while the MMAs run
-            const int ten4 = sTen / CH;
+            const int ten4 = NPN * S / CH;
             for (int e = tid; e < ten4; e += blockDim.x) reinterpret_cast<uint4*>(U)[e] = make_uint4(0u, 0u, 0u, 0u);
             if (tid == 0 && !mbar_wait(bar, phase, kWaitLimitNs)) sFail = 1;
             phase ^= 1;
@@ -415,7 +413,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                         for (int yy = 0; yy < N; ++yy)
 #pragma unroll
                             for (int xx = 0; xx < N; ++xx)
-                                atomicAdd(&U[base + ((z * NP + yy) * NP + xx) * ld], y[(z * N + yy) * N + xx]);
+                                atomicAdd(&U[base + ((z * NP + yy) * NP + xx) * S], y[(z * N + yy) * N + xx]);
                 }
             }
             tc_fence_before();
@@ -430,7 +428,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                 const int32_t o = sOff[bb][ne >> 16];
                 if (o < 0) continue;
                 const int ldb = sLd[bb];
-                const float* ys = U + sBase[bb] + node * ldb;
+                const float* ys = U + node * S + sBase[bb];
                 float* yd = a.Y + (int64_t)o * 4 + (ne & 0xffff) * ldb;
                 for (int c0 = 0; c0 < ldb; c0 += CH) {
                     const float4 f = *reinterpret_cast<const float4*>(ys + c0);
