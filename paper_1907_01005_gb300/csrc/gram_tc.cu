@@ -384,24 +384,45 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
             }
         }
         // ---- flush: exact window value into the int64 accumulators -----------
-        int dRa[2], dWa[2];
+        // In units of 2^-(8 LMAX) the window value is
+        //   t = i2 2^(8 LMAX - 16) + i3 2^(8 LMAX - 24) + hi 2^(4 LMAX) + lo
+        // (i2, i3: the exact level-2 / level-3 sums; hi, lo: the levels-4+ sum
+        // rounded on the 2^-(4 LMAX) grid and its remainder).  The first three
+        // share the factor 2^(4 LMAX) and their sum fits in 32 bits
+        // (|i2| <= 2^22 x 2^8, |i3| <= 2^23, |hi| <= 2^16 for P^T P; |i2| <= 2^23,
+        // |hi| <= 2^15 for P^T Y), so t is one 32-bit sum shifted, plus lo.
+        int dRa[2], dWa[2], dRb[8], dWb[8];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             dRa[h] = sDR[0][wm + gid + 8 * h];
             dWa[h] = sDW[0][wm + gid + 8 * h];
         }
+        int grow = dRa[0] | dRa[1];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int n = wn + 8 * (q >> 1) + 2 * tig + (q & 1);
+            dRb[q] = sDR[bo][n];
+            dWb[q] = sDW[bo][n];
+            grow |= dRb[q];
+        }
+        // the reference exponents grow in few windows: shift the accumulators
+        // only when some lane of the warp needs it
+        const bool any_grow = __any_sync(0xffffffffu, grow != 0);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const int n = wn + 8 * j + 2 * tig + (v & 1);
+                const int q = 2 * j + (v & 1);
                 const int h = v >> 1;
-                const long long i2 = __float2int_rn(wacc[0][j][v] * pow2f(16));
-                const long long iR = round_scaled_i64<8 * LMAX, 4 * LMAX>(wacc[2][j][v]);
-                long long t = (i2 << (8 * (LMAX - 2))) + iR;
-                if constexpr (!NAT) t += (long long)__float2int_rn(wacc[1][j][v] * pow2f(24)) << (8 * (LMAX - 3));
-                const int shR = min(dRa[h] + sDR[bo][n], 63), shW = min(dWa[h] + sDW[bo][n], 63);
-                acc[j][v] = (acc[j][v] >> shR) + (t >> shW);
+                const float w2 = wacc[2][j][v];
+                const float hiF = rintf(w2 * pow2f(4 * LMAX));
+                const int lo = __float2int_rn(fmaf(-hiF, pow2f(-4 * LMAX), w2) * pow2f(8 * LMAX));
+                int top = (__float2int_rn(wacc[0][j][v] * pow2f(16)) << (4 * LMAX - 16)) + (int)hiF;
+                if constexpr (!NAT) top += __float2int_rn(wacc[1][j][v] * pow2f(24)) << (4 * LMAX - 24);
+                const long long t = ((long long)top << (4 * LMAX)) + lo;
+                const int shW = min(dWa[h] + dWb[q], 63);
+                if (any_grow) acc[j][v] >>= min(dRa[h] + dRb[q], 63);
+                acc[j][v] += t >> shW;
             }
     }
     if (!wact) return;
