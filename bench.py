@@ -235,9 +235,9 @@ _SRC_GRAM = ("gram_tc.cu",)
 _SRC_APPLY = ("apply_unit.cu", "unit_common.cuh")
 _SRC_MMULT = ("mmult.cu",)
 NCU_TRAFFIC = {
-    "gram_py": (_SRC_GRAM, "2f73977a3ff2127e2a1418246419ed76d1a583468eaad8f4b343ff72c8ecb8ef", 508275968),
-    "gram_pp": (_SRC_GRAM, "2f73977a3ff2127e2a1418246419ed76d1a583468eaad8f4b343ff72c8ecb8ef", 256380928),
-    "apply": (_SRC_APPLY, "97d1b663b1c66bfbb458480b05dfe46bfc2da0190b77dd07c0ef70819fff92b4", 665428736),
+    "gram_py": (_SRC_GRAM, "3545e777a29d01b9740366ede465023c1a69c4a108ea1358b88315f3ec9e5e2a", 508486400),
+    "gram_pp": (_SRC_GRAM, "3545e777a29d01b9740366ede465023c1a69c4a108ea1358b88315f3ec9e5e2a", 256353792),
+    "apply": (_SRC_APPLY, "1bc773a6ea92c9c0e9577d57bd3794cc843d694a80dbe30c5f744119779ed9bc", 655558912),
     "mmult": (_SRC_MMULT, "1ba37459ab68dc9c047f3d4afc08675456773d90c7df21aa698aea12cea384b5", 706672384),
 }
 
