@@ -582,10 +582,13 @@ def main():
         k64 = max(3, args.steps // 5)
         tot64, per64 = time_path(pb64, k64, max(3, args.warmup // 2))
         ms64 = max_over_ranks(tot64 / k64, world)
+        a64, py64, pp64 = (statistics.median(per64[k]) for k in ("apply", "gram_py", "gram_pp"))
         line["fp64"] = {"ms_per_step": ms64, "value": world * N * M / (ms64 * 1e-3),
-                        "apply_ms": statistics.median(per64["apply"]),
-                        "gram_py_ms": statistics.median(per64["gram_py"]),
-                        "gram_pp_ms": statistics.median(per64["gram_pp"]),
+                        "p50_ms": pct(per64["step"], 0.5), "p99_ms": pct(per64["step"], 0.99),
+                        "apply_ms": a64, "gram_py_ms": py64, "gram_pp_ms": pp64,
+                        "apply_dof_cols_per_s": N * M / (a64 * 1e-3),
+                        "gram_gflops": {"PtY": info.gram_flops / (py64 * 1e-3) / 1e9,
+                                        "PtP": info.gram_flops / (pp64 * 1e-3) / 1e9},
                         "mixed_speedup": ms64 / ms_step}
         del pb64
         torch.cuda.empty_cache()
