@@ -94,8 +94,12 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) 
 // chunk) and with bit 3 of the chunk index moved to bit 1 (a staging store
 // phase writes 2 columns x 4 row segments, whose chunks differ in bits 2
 // and 3): both patterns hit 8 different 16-byte bank groups.
-template <int KW>
+// With NSEG = 8 row segments of two chunks, bit 3 of the chunk index goes to
+// bit 0 instead: the 8 segments of one column, which store together, then
+// also hit 8 different bank groups.
+template <int KW, int NSEG = 4>
 __device__ __forceinline__ unsigned chunk_off(int c, int kc) {
+    if constexpr (NSEG == 8) return (unsigned)(c * (KW * 2) + ((kc ^ (c & 7) ^ ((kc >> 3) & 1)) << 4));
     return (unsigned)(c * (KW * 2) + ((kc ^ (c & 7) ^ (((kc >> 3) & 1) << 1)) << 4));
 }
 
@@ -183,7 +187,7 @@ __device__ __forceinline__ WinExp window_exponent(float mx, int& R) {
 
 // Slices a thread's SEG values (column c, rows seg*SEG ..) into S bf16
 // slices y_s = q_s 2^(-8 s) and stores them as SEG/8 16-byte chunks each.
-template <int S, int SEG, int KW>
+template <int S, int SEG, int KW, int NSEG = 4>
 __device__ __forceinline__ void slice_store(unsigned char* base, int c, int seg, float f1, float f2,
                                             const float (&v)[SEG]) {
     constexpr int SLICE = kST * KW * 2;
@@ -192,7 +196,7 @@ __device__ __forceinline__ void slice_store(unsigned char* base, int c, int seg,
         float r[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) r[i] = (v[ch * 8 + i] * f1) * f2;
-        const unsigned off = chunk_off<KW>(c, seg * (SEG / 8) + ch);
+        const unsigned off = chunk_off<KW, NSEG>(c, seg * (SEG / 8) + ch);
 #pragma unroll
         for (int s = 1; s <= S; ++s) {
             const float up = pow2f(8 * s), dn = pow2f(-8 * s);
@@ -214,13 +218,13 @@ __device__ __forceinline__ void slice_store(unsigned char* base, int c, int seg,
 // y2 = bf16(x - y1), y3 = bf16(x - y1 - y2).  Products y1 y1' stay on the
 // 2^-16 grid (exact window sums); the others are exact FP32 numbers whose
 // window sums are rounded, at a weight of 2^-8 of the result or less.
-template <int SEG, int KW>
+template <int SEG, int KW, int NSEG = 4>
 __device__ __forceinline__ void slice_store_nat(unsigned char* base, int c, int seg, float f1, float f2,
                                                 const float (&v)[SEG]) {
     constexpr int SLICE = kST * KW * 2;
 #pragma unroll
     for (int ch = 0; ch < SEG / 8; ++ch) {
-        const unsigned off = chunk_off<KW>(c, seg * (SEG / 8) + ch);
+        const unsigned off = chunk_off<KW, NSEG>(c, seg * (SEG / 8) + ch);
         uint32_t w1[4], w2[4], w3[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -247,7 +251,12 @@ template <int SA, int SB, int LMAX, bool SYM, bool SAME, int KW, bool NAT>
 __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g) {
     static_assert(KW % 32 == 0 && KW <= 128, "window rows");
     static_assert(!NAT || (SA == 3 && SB == 3), "natural slices: three per operand");
-    constexpr int SEG = KW / 4;                   // rows per staging thread
+    // staging: NSEG lanes per column, SEG rows each; 128-row windows take
+    // two passes of 32 columns (16 rows a lane keeps the registers in bounds)
+    constexpr int NSEG = KW >= 128 ? 8 : 4;
+    constexpr int SEG = KW / NSEG;                // rows per staging thread
+    constexpr int CPP = kThreads / NSEG;          // columns per pass
+    constexpr int NPASS = kST / CPP;
     constexpr int SLICE = kST * KW * 2;           // bytes per staged slice
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* As = smem;
@@ -298,8 +307,10 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
     const int wm = (warp >> 1) * 16, wn = (warp & 1) * 32;
     const int gid = lane >> 2, tig = lane & 3;
     const bool wact = (mi * kST + wm < gr.width) && (ni * kST + wn < gr.width) && (!diag || wm < wn + 32);
-    const int c = tid >> 2, seg = tid & 3;        // staging: a column's four row segments sit in one warp
-    int RA = kNone, RB = kNone;                   // running reference exponents of this thread's column
+    const int seg = tid % NSEG;                   // a column's NSEG row segments sit in one warp
+    int RA[NPASS], RB[NPASS];                     // running reference exponents of this thread's columns
+#pragma unroll
+    for (int ps = 0; ps < NPASS; ++ps) RA[ps] = RB[ps] = kNone;
 
     long long acc[4][4];
 #pragma unroll
@@ -312,39 +323,43 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
 
     for (int k0 = it.k0; k0 < it.k1; k0 += KW) {
         __syncthreads();                           // tables ready; previous window's MMAs and flush done
-        // ---- per operand: load, column bound (4 lanes of a column), slices ----
-        {
-            const int ca = sColA[c];
-            float v[SEG];
-            float mx = load_window<SEG>(g.A, ca, sOff, gr.n_u, sPref, nrb, k0 + seg * SEG, it.k1, v);
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-            const WinExp e = window_exponent(mx, RA);
-            if (seg == 0) {
-                sDR[0][c] = e.dR;
-                sDW[0][c] = e.dW;
-                sR[0][c] = RA;
+        // ---- per operand: load, column bound (NSEG lanes of a column), slices
+#pragma unroll
+        for (int ps = 0; ps < NPASS; ++ps) {
+            const int c = ps * CPP + tid / NSEG;
+            {
+                const int ca = sColA[c];
+                float v[SEG];
+                float mx = load_window<SEG>(g.A, ca, sOff, gr.n_u, sPref, nrb, k0 + seg * SEG, it.k1, v);
+#pragma unroll
+                for (int o = 1; o < NSEG; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                const WinExp e = window_exponent(mx, RA[ps]);
+                if (seg == 0) {
+                    sDR[0][c] = e.dR;
+                    sDW[0][c] = e.dW;
+                    sR[0][c] = RA[ps];
+                }
+                if (ca >= 0) {
+                    if constexpr (NAT) slice_store_nat<SEG, KW, NSEG>(As, c, seg, e.f1, e.f2, v);
+                    else slice_store<SA, SEG, KW, NSEG>(As, c, seg, e.f1, e.f2, v);
+                }
             }
-            if (ca >= 0) {
-                if constexpr (NAT) slice_store_nat<SEG, KW>(As, c, seg, e.f1, e.f2, v);
-                else slice_store<SA, SEG, KW>(As, c, seg, e.f1, e.f2, v);
-            }
-        }
-        if (!share) {
-            const int cb = sColB[c];
-            float v[SEG];
-            float mx = load_window<SEG>(g.B, cb, sOff, gr.n_u, sPref, nrb, k0 + seg * SEG, it.k1, v);
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-            const WinExp e = window_exponent(mx, RB);
-            if (seg == 0) {
-                sDR[1][c] = e.dR;
-                sDW[1][c] = e.dW;
-                sR[1][c] = RB;
-            }
-            if (cb >= 0) {
-                if constexpr (NAT) slice_store_nat<SEG, KW>(Bs, c, seg, e.f1, e.f2, v);
-                else slice_store<SB, SEG, KW>(Bs, c, seg, e.f1, e.f2, v);
+            if (!share) {
+                const int cb = sColB[c];
+                float v[SEG];
+                float mx = load_window<SEG>(g.B, cb, sOff, gr.n_u, sPref, nrb, k0 + seg * SEG, it.k1, v);
+#pragma unroll
+                for (int o = 1; o < NSEG; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                const WinExp e = window_exponent(mx, RB[ps]);
+                if (seg == 0) {
+                    sDR[1][c] = e.dR;
+                    sDW[1][c] = e.dW;
+                    sR[1][c] = RB[ps];
+                }
+                if (cb >= 0) {
+                    if constexpr (NAT) slice_store_nat<SEG, KW, NSEG>(Bs, c, seg, e.f1, e.f2, v);
+                    else slice_store<SB, SEG, KW, NSEG>(Bs, c, seg, e.f1, e.f2, v);
+                }
             }
         }
         __syncthreads();
@@ -364,10 +379,10 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const GramTcArgs g
         for (int ks = 0; ks < KW / 16; ++ks) {
             uint32_t af[SA][4];
 #pragma unroll
-            for (int s = 0; s < SA; ++s) ldsm_x4(af[s], As_s + s * SLICE + chunk_off<KW>(am, 2 * ks + (lane >> 4)));
+            for (int s = 0; s < SA; ++s) ldsm_x4(af[s], As_s + s * SLICE + chunk_off<KW, NSEG>(am, 2 * ks + (lane >> 4)));
 #pragma unroll
             for (int p = 0; p < 2; ++p) {                 // pairs of n8 tiles
-                const unsigned boff = chunk_off<KW>(bn + 16 * p, 2 * ks + ((lane >> 3) & 1));
+                const unsigned boff = chunk_off<KW, NSEG>(bn + 16 * p, 2 * ks + ((lane >> 3) & 1));
 #pragma unroll
                 for (int t = 1; t <= SB; ++t) {            // one B slice at a time
                     uint32_t bf[4];
