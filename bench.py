@@ -235,8 +235,8 @@ _SRC_GRAM = ("gram_tc.cu",)
 _SRC_APPLY = ("apply_unit.cu", "unit_common.cuh")
 _SRC_MMULT = ("mmult.cu",)
 NCU_TRAFFIC = {
-    "gram_py": (_SRC_GRAM, "3545e777a29d01b9740366ede465023c1a69c4a108ea1358b88315f3ec9e5e2a", 508486400),
-    "gram_pp": (_SRC_GRAM, "3545e777a29d01b9740366ede465023c1a69c4a108ea1358b88315f3ec9e5e2a", 256353792),
+    "gram_py": (_SRC_GRAM, "78e17e1c22840b51c1d9803fcb618979de9234a529c23c5e4cc0ab58c954ebfb", 506702080),
+    "gram_pp": (_SRC_GRAM, "78e17e1c22840b51c1d9803fcb618979de9234a529c23c5e4cc0ab58c954ebfb", 256430848),
     "apply": (_SRC_APPLY, "1bc773a6ea92c9c0e9577d57bd3794cc843d694a80dbe30c5f744119779ed9bc", 655558912),
     "mmult": (_SRC_MMULT, "1ba37459ab68dc9c047f3d4afc08675456773d90c7df21aa698aea12cea384b5", 706672384),
 }
