@@ -279,12 +279,13 @@ def serving_config(index: int, mesh: tuple, p: int, n_orb: int, fill: float) -> 
 
 def serving_mix(n: int, seed: int = SEED_BASE + 7, meshes=SERVING_MESHES, degrees=(2, 4),
                 orb_range=(32, 640), fill_range=(0.10, 0.30)):
-    """n request workloads drawn from the serving mix: mesh and degree
-    uniform over the given sets, orbital count log-uniform, fill uniform."""
+    """n request workloads drawn from the serving mix: the meshes taken in
+    turn (so that a small pool holds every mesh size), degree uniform over
+    the given set, orbital count log-uniform, fill uniform."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
-        mesh = meshes[int(rng.integers(len(meshes)))]
+        mesh = meshes[i % len(meshes)]
         p = int(degrees[int(rng.integers(len(degrees)))])
         m = int(round(math.exp(rng.uniform(math.log(orb_range[0]), math.log(orb_range[1])))))
         f = float(rng.uniform(*fill_range))
