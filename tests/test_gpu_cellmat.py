@@ -169,3 +169,37 @@ def test_cellmat_paper_scale_p2():
     assert _relerr(np.array(got), np.array(ref)) <= TOL["Y"]
     ref_pp = O.gram(Psp, Psp)[np.ix_(pb.perm, pb.perm)]
     assert _relerr(d["G_PP"].cpu().numpy(), ref_pp) <= TOL["PP"]
+
+
+def test_cellmat_in_graph_and_host_entry():
+    """The cell-matrix form inside a captured CUDA graph of the step and
+    through the host-buffer entry point gives the eager device step's result
+    (up to the order of the atomic additions)."""
+    import torch
+    from paper_1907_01005_gb300 import StepGraph, apply_H_gram, apply_H_gram_host
+    cfg, pb = _problem("small_p2")
+    d = pb.dev
+    apply_H_gram(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"])
+    torch.cuda.synchronize()
+    Y0, Gpy0, Gpp0 = d["Y"].cpu().numpy(), d["G_PY"].cpu().numpy(), d["G_PP"].cpu().numpy()
+    g = StepGraph(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"])
+    d["Y"].zero_()
+    d["G_PY"].zero_()
+    g.launch()
+    g.launch()                               # replays reset the work counter and Y
+    torch.cuda.synchronize()
+    assert pb.mesh.check_device() == 0
+    assert _relerr(d["Y"].cpu().numpy(), Y0) <= 1e-6
+    assert _relerr(d["G_PY"].cpu().numpy(), Gpy0) <= 1e-6
+    assert _relerr(d["G_PP"].cpu().numpy(), Gpp0) <= 1e-14
+    del g
+    M = pb.n_cols
+    Ph = torch.from_numpy(pb.P_host.copy()).pin_memory()
+    Yh = torch.zeros(d["Y"].shape, dtype=d["Y"].dtype).pin_memory()
+    G1 = torch.zeros((M, M), dtype=torch.float64).pin_memory()
+    G2 = torch.zeros((M, M), dtype=torch.float64).pin_memory()
+    apply_H_gram_host(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], Ph, Yh, G1, G2)
+    assert pb.mesh.check_device() == 0
+    assert _relerr(Yh.numpy(), Y0) <= 1e-6
+    assert _relerr(G1.numpy(), Gpy0) <= 1e-6
+    assert _relerr(G2.numpy(), Gpp0) <= 1e-14

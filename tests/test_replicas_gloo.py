@@ -64,3 +64,4 @@ def test_bench_parses_and_clock_sampler_degrades_without_gpu():
     c.start()
     res = c.stop()
     assert "reasons" in res and "sm_mhz" in res
+
