@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Benchmark of the hot path: Y = mask(P) * (H P), P^T Y and P^T P.
 
-One step = fe_apply_H + fe_gram_PtY + fe_gram_PtP on the paper-scale p=2
+One step = fe_apply_H_gram (apply, P^T Y, P^T P) on the paper-scale p=2
 workload (64x40x40 Q2 cells, 846,369 DoFs x 320 orbitals in 38 column
 blocks, ~20% block fill), FP32 cell arithmetic with FP64 Gram accumulation;
 the FP64 path is timed beside it.  Inputs are resident in HBM when the timed
@@ -268,7 +268,10 @@ def time_path(pb, steps, warmup):
     fe_apply_H_gram (P^T P overlapped with the apply), then `steps` runs of the
     three calls one after another for the per-kernel breakdown."""
     import torch
-    from paper_1907_01005_gb300 import apply_H, apply_H_gram, gram_PtP, gram_PtY
+    from paper_1907_01005_gb300 import apply_H, apply_H_gram, gram_PtP, gram_PtY, gram_PtY_sym
+    # the step forms P^T Y in its symmetric form on a closed pattern (upper
+    # blocks, mirrored); the breakdown times the same form
+    pty = gram_PtY_sym if pb.P.get_closed() else gram_PtY
     d = pb.dev
     s = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -288,7 +291,7 @@ def time_path(pb, steps, warmup):
         e[0].record(s)
         apply_H(pb.mesh, pb.P, pb.Y, s)
         e[1].record(s)
-        gram_PtY(pb.P, pb.Y, d["G_PY"], s)
+        pty(pb.P, pb.Y, d["G_PY"], s)
         e[2].record(s)
         gram_PtP(pb.P, d["G_PP"], s)
         e[3].record(s)
@@ -351,7 +354,7 @@ def time_om(pb, steps):
     workload (Sec. 2): Phi_M = M P, Mbar = P^T Phi_M, the two post-
     multiplications of the gradient and tr(D^T G); CUDA-event medians (ms)."""
     import torch
-    from paper_1907_01005_gb300 import BCSR, apply_M, gram_PtY, mmult, trace_dot
+    from paper_1907_01005_gb300 import BCSR, apply_M, gram_PtY_sym, mmult, trace_dot
     d = pb.dev
     M = pb.n_cols
 
@@ -366,7 +369,7 @@ def time_om(pb, steps):
     g = torch.zeros(1, dtype=torch.float64, device="cuda")
     s = torch.cuda.current_stream()
     names = ("apply_M", "gram_M", "mmult_1", "mmult_2", "trace")
-    calls = (lambda: apply_M(pb.mesh, pb.P, YM, s), lambda: gram_PtY(pb.P, YM, Mb, s),
+    calls = (lambda: apply_M(pb.mesh, pb.P, YM, s), lambda: gram_PtY_sym(pb.P, YM, Mb, s),
              lambda: mmult(pb.Y, Mb, G, -2.0, -2.0, 0.0, s), lambda: mmult(YM, d["G_PY"], G, -2.0, 0.0, 1.0, s),
              lambda: trace_dot(D, G, g, s))
     for _ in range(3):

@@ -237,16 +237,28 @@ int fe_apply_M(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, void* stream);
 /* G = P^T Y (Alg. 8, Eq. inner2): dense n_cols x n_cols FP64, row-major, in
  * the column order of the multivectors, zero where no row block holds both
  * column blocks.  G_dev is caller-owned device memory (n_cols^2 doubles);
- * it is overwritten.  Accumulation is FP64 whatever the dtype. */
+ * it is overwritten.  Accumulation is FP64 whatever the dtype.  Every block
+ * of the product is formed, whatever Y holds. */
 int fe_gram_PtY(const fe_bcsr* P, const fe_bcsr* Y, double* G_dev, void* stream);
+
+/* The same product when the caller knows it to be symmetric: Y holds H P or
+ * M P (fe_apply_H / fe_apply_M) of P's current values, and P's pattern is
+ * closed for them (fe_bcsr_set_closed), so that mask(P) * (H P) = H P and
+ * P^T Y = P^T H P (Eq. inner2; likewise P^T M P, Eq. inner1).  Only the
+ * blocks c1 <= c2 are formed and mirrored, about half the work.  FE_ESTATE
+ * if P is not declared closed.  For any other Y the result is wrong: use
+ * fe_gram_PtY. */
+int fe_gram_PtY_sym(const fe_bcsr* P, const fe_bcsr* Y, double* G_dev, void* stream);
 
 /* G = P^T P (Alg. 8 / Eq. inner1 with the Euclidean product), same layout;
  * computed for column-block pairs c1 <= c2 and mirrored. */
 int fe_gram_PtP(const fe_bcsr* P, double* G_dev, void* stream);
 
-/* fe_apply_H then fe_gram_PtY on `stream`, and fe_gram_PtP (which does not
+/* fe_apply_H then P^T Y on `stream`, and fe_gram_PtP (which does not
  * read Y) concurrently on a side stream owned by P, forked from `stream`
- * before the apply and joined back after fe_gram_PtY with events; all work
+ * before the apply and joined back after P^T Y with events.  Y is formed
+ * from P in the same call, so P^T Y takes the symmetric form of
+ * fe_gram_PtY_sym when P is declared closed, else that of fe_gram_PtY.  All work
  * is ordered after earlier work on `stream` and before later work on it
  * (stream capture of the call records the fork and the join).  The side
  * stream is created on the first call and destroyed with P. */
@@ -316,10 +328,12 @@ int fe_bcsr_get_launch(const fe_bcsr* P, int32_t* persistent, int32_t* ctas_per_
  * for the values P will hold: every row block that owns a node of a cell
  * touching the support of a column block is in that column block's pattern
  * (fe_pattern_closed builds such patterns, Sec. 3.5 reading).  Then
- * mask(P) * (H P) = H P, so P^T Y = P^T H P is symmetric, and fe_gram_PtY and
- * fe_apply_H_gram compute its upper blocks only and mirror them.  Declaring
- * it for a pattern that is not closed gives a wrong P^T Y.  FE_EINVAL for a
- * flag other than 0 or 1. */
+ * mask(P) * (H P) = H P, so P^T H P is symmetric: fe_apply_H_gram (and the
+ * host-buffer variant and the graph of the step), which form Y = H P
+ * themselves, compute its upper blocks only and mirror them, and
+ * fe_gram_PtY_sym becomes available.  fe_gram_PtY is not affected.
+ * Declaring it for a pattern that is not closed gives a wrong P^T Y in those
+ * calls.  FE_EINVAL for a flag other than 0 or 1. */
 int fe_bcsr_set_closed(fe_bcsr* P, int32_t closed);
 int fe_bcsr_get_closed(const fe_bcsr* P, int32_t* closed);
 
@@ -375,25 +389,33 @@ int fe_autotune(fe_mesh* mesh, fe_bcsr* P, fe_bcsr* Y, const char* cache_path, v
 /* Runs an FMA-throughput probe on the current device (dtype FE_F32, FE_F64,
  * or 3 for packed FP32x2 FMA; eight independent chains per thread, 8 CTAs of
  * 256 threads per SM, `iters` x 128 FMAs per thread) and returns the achieved
- * flop/s (2 per FMA),
- * the ALU peak used for the roofline of ALU-bound kernels.  Synchronises
- * `stream`; uses a small stream-ordered allocation. */
+ * flop/s (2 per FMA), the ALU peak used for the roofline of ALU-bound
+ * kernels.  Thread 0 of every CTA stores its chain sum in the CTA's slot of
+ * a sink; the call reads the first and last slot back and returns
+ * FE_EDEVICE if they differ from the sum the host computes with the same
+ * fused multiply-adds.  Synchronises `stream` (so it cannot be captured in
+ * a CUDA graph); uses a small stream-ordered allocation for the sink. */
 int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream);
 
 /* Allocation-free variant of fe_probe_fma (the paper has no counterpart: it
- * is a measurement helper).  Same arguments, kernels and result; the per-CTA
- * sink of the chains lives in a static device array of 4096 doubles (32 KB)
- * instead of a stream-ordered allocation, so the call allocates no device
- * memory at all.  For callers that may not allocate, such as a server that
- * has admitted work up to its device-memory budget.
- *   - The first call on each device does a one-time set-up (it resolves the
- *     array's device address with that device current); make that first call
- *     before any stream capture.
+ * is a measurement helper).  Same arguments, kernels, check and result; the
+ * per-CTA sink lives in a static device array of 4096 doubles (32 KB) that
+ * every GPU which loads the library holds until the process exits, instead
+ * of a stream-ordered allocation, so the call allocates no device memory at
+ * all.  For callers that may not allocate, such as a server that has
+ * admitted work up to its device-memory budget.
+ *   - The first call on each device does a one-time set-up: with that
+ *     device current it resolves the array's device address.  Like every
+ *     call, it synchronises `stream`, so no call may be issued while a
+ *     stream capture is in progress.
+ *   - The slots are read back through the array's symbol, not through the
+ *     resolved address, so a wrong address gives FE_EDEVICE.
  *   - FE_EINVAL with a message when the device needs more than 4096 slots
  *     (8 per SM, i.e. more than 512 SMs) or its ordinal is 64 or more.
  *   - All calls share the array, which keeps the last contents; nothing in
- *     it needs to start at zero.  Overlapping calls (other streams or host
- *     threads) race on its contents. */
+ *     it needs to start at zero (each CTA writes its own slot before the
+ *     read-back).  Calls that overlap on the GPU (other streams or host
+ *     threads) race on its contents and may fail the check. */
 int fe_probe_fma_static(int32_t dtype, int64_t iters, double* flops_per_s, void* stream);
 
 #ifdef __cplusplus

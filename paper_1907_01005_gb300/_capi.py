@@ -84,6 +84,7 @@ SIGNATURES = {
     "fe_apply_H": [_P, _P, _P, _P],
     "fe_apply_M": [_P, _P, _P, _P],
     "fe_gram_PtY": [_P, _P, _P, _P],
+    "fe_gram_PtY_sym": [_P, _P, _P, _P],
     "fe_gram_PtP": [_P, _P, _P],
     "fe_apply_H_gram": [_P, _P, _P, _P, _P, _P],
     "fe_apply_H_gram_host": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],

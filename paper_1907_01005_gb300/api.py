@@ -219,7 +219,14 @@ def apply_M(mesh: Mesh, P: BCSR, Y: BCSR, stream=None):
 
 
 def gram_PtY(P: BCSR, Y: BCSR, G, stream=None):
+    """G = P^T Y, every block formed."""
     check(capi.fe_gram_PtY(P.h, Y.h, _dptr(G), _stream(stream)))
+
+
+def gram_PtY_sym(P: BCSR, Y: BCSR, G, stream=None):
+    """G = P^T Y when the caller knows it is symmetric (Y = H P or M P of P's
+    current values, P declared closed): upper blocks formed and mirrored."""
+    check(capi.fe_gram_PtY_sym(P.h, Y.h, _dptr(G), _stream(stream)))
 
 
 def gram_PtP(P: BCSR, G, stream=None):

@@ -260,10 +260,13 @@ cudaError_t launch_mmult(const MmultArgs<T>& a, float* x_round, cudaStream_t s);
 template <typename T>
 cudaError_t launch_trace(const TraceArgs<T>& a, cudaStream_t s);
 
-cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s);
+// *sink_ok: the first and last CTA slot of the sink hold thread 0's chain sum
+// as the host computes it
+cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s, bool* sink_ok);
 constexpr int kProbeSinkSlots = 4096;   // per-CTA slots of the allocation-free probe (512 SMs x 8)
 // *too_many: 0 = ran; > 0 = the device needs that many slots (> kProbeSinkSlots);
-// -1 = device ordinal beyond the per-device table
+// -1 = device ordinal beyond the per-device table; -2 = the static sink,
+// read back through its symbol, does not hold the chain sums
 cudaError_t probe_fma_static(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s, int* too_many);
 
 // Device status codes written by kernels.

@@ -1192,14 +1192,29 @@ int fe_apply_H(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, void* stream) {
     return P->dtype == FE_F64 ? apply_impl<double>(m, P, Y, s) : apply_impl<float>(m, P, Y, s);
 }
 
-int fe_gram_PtY(const fe_bcsr* P, const fe_bcsr* Y, double* G, void* stream) {
-    int rc = check_pair("fe_gram_PtY", nullptr, P, Y);
+}  // extern "C"
+
+namespace {
+// P^T Y; `sym`: the caller knows the product is symmetric (Y = H P or M P
+// on a pattern closed for P's values), so only the upper blocks are formed
+int gram_pty(const char* fn, const fe_bcsr* P, const fe_bcsr* Y, double* G, bool sym, cudaStream_t s) {
+    int rc = check_pair(fn, nullptr, P, Y);
     if (rc) return rc;
-    if (!G) return fail(FE_EINVAL, "fe_gram_PtY: G is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
-    // a closed pattern makes P^T Y = P^T H P symmetric: upper blocks, mirrored
-    const bool sym = P->closed != 0;
+    if (!G) return fail(FE_EINVAL, "%s: G is NULL", fn);
     return P->dtype == FE_F64 ? gram_impl<double>(P, Y, sym, G, s) : gram_impl<float>(P, Y, sym, G, s);
+}
+}  // namespace
+
+extern "C" {
+
+int fe_gram_PtY(const fe_bcsr* P, const fe_bcsr* Y, double* G, void* stream) {
+    return gram_pty("fe_gram_PtY", P, Y, G, false, (cudaStream_t)stream);
+}
+
+int fe_gram_PtY_sym(const fe_bcsr* P, const fe_bcsr* Y, double* G, void* stream) {
+    if (P && !P->closed)
+        return fail(FE_ESTATE, "fe_gram_PtY_sym: P's pattern is not declared closed (fe_bcsr_set_closed)");
+    return gram_pty("fe_gram_PtY_sym", P, Y, G, true, (cudaStream_t)stream);
 }
 
 int fe_gram_PtP(const fe_bcsr* P, double* G, void* stream) {
@@ -1236,7 +1251,9 @@ int fe_apply_H_gram(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY, doub
     const int rc_pp = fe_gram_PtP(P, G_PP, Pm->side);
     FE_TRY_CUDA(cudaEventRecord(Pm->ev_join, Pm->side), "fe_apply_H_gram: join");
     rc = fe_apply_H(m, P, Y, stream);
-    if (rc == FE_OK) rc = fe_gram_PtY(P, Y, G_PY, stream);
+    // Y = H P was formed from P's values just now: on a closed pattern P^T Y
+    // is symmetric and its upper blocks suffice
+    if (rc == FE_OK) rc = gram_pty("fe_apply_H_gram", P, Y, G_PY, P->closed != 0, s);
     FE_TRY_CUDA(cudaStreamWaitEvent(s, Pm->ev_join, 0), "fe_apply_H_gram: join");
     return rc != FE_OK ? rc : rc_pp;
 }
@@ -1272,7 +1289,7 @@ int fe_apply_H_gram_host(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY,
         FE_TRY_CUDA(cudaStreamWaitEvent(Pm->copy, Pm->ev_y, 0), "fe_apply_H_gram_host: Y ready");
         FE_TRY_CUDA(cudaMemcpyAsync(Y_host, Y->values, vb, cudaMemcpyDeviceToHost, Pm->copy), "fe_apply_H_gram_host: copy Y out");
         FE_TRY_CUDA(cudaEventRecord(Pm->ev_copied, Pm->copy), "fe_apply_H_gram_host: Y copied");
-        rc = fe_gram_PtY(P, Y, G_PY, stream);
+        rc = gram_pty("fe_apply_H_gram_host", P, Y, G_PY, P->closed != 0, s);
         if (rc == FE_OK)
             FE_TRY_CUDA(cudaMemcpyAsync(G_PY_host, G_PY, gb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy G_PY out");
         FE_TRY_CUDA(cudaStreamWaitEvent(s, Pm->ev_copied, 0), "fe_apply_H_gram_host: join copy");
@@ -1285,7 +1302,9 @@ int fe_apply_H_gram_host(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY,
 int fe_probe_fma(int32_t dtype, int64_t iters, double* flops_per_s, void* stream) {
     if (!flops_per_s || iters < 1 || (dtype != FE_F32 && dtype != FE_F64 && dtype != 3))
         return fail(FE_EINVAL, "fe_probe_fma: bad argument");
-    FE_TRY_CUDA(probe_fma(dtype, iters, flops_per_s, (cudaStream_t)stream), "fe_probe_fma");
+    bool sink_ok = false;
+    FE_TRY_CUDA(probe_fma(dtype, iters, flops_per_s, (cudaStream_t)stream, &sink_ok), "fe_probe_fma");
+    if (!sink_ok) return fail(FE_EDEVICE, "fe_probe_fma: the sink does not hold the chain sums the host computes");
     return FE_OK;
 }
 
@@ -1299,8 +1318,11 @@ int fe_probe_fma_static(int32_t dtype, int64_t iters, double* flops_per_s, void*
         return fail(FE_EINVAL,
                     "fe_probe_fma_static: this device needs %d per-CTA sink slots (8 per SM); the static "
                     "sink holds %d (devices of up to %d SMs)", too_many, kProbeSinkSlots, kProbeSinkSlots / 8);
-    if (too_many < 0)
+    if (too_many == -1)
         return fail(FE_EINVAL, "fe_probe_fma_static: device ordinal beyond the 64 devices the set-up table holds");
+    if (too_many == -2)
+        return fail(FE_EDEVICE, "fe_probe_fma_static: the static sink, read back through its symbol, does not "
+                                "hold the chain sums the host computes");
     return FE_OK;
 }
 

@@ -2,6 +2,8 @@
 // cell kernels and of the FP64 Gram is reported against.  Each thread runs
 // eight independent FMA chains so that latency is hidden; the grid covers
 // every SM several times.
+#include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "fe_internal.h"
@@ -21,7 +23,10 @@ __global__ void __launch_bounds__(256) fma_chains(T* out, int64_t iters, T a, T 
         }
     }
     const T s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
-    if (s == T(-1.2345)) out[blockIdx.x] = s;   // keeps the chains alive
+    // thread 0 records its sum in the CTA's slot (every CTA runs the same
+    // chains, so every slot gets the same value, which the host checks);
+    // the compare keeps the other threads' chains alive
+    if (threadIdx.x == 0 || s == T(-1.2345)) out[blockIdx.x] = s;
 }
 
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
@@ -48,38 +53,87 @@ __global__ void __launch_bounds__(256) fma2_chains(float* out, int64_t iters, fl
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) s += x[c].x + x[c].y;
-    if (s == -1.2345f) out[blockIdx.x] = s;
+    if (threadIdx.x == 0 || s == -1.2345f) out[blockIdx.x] = s;
 }
 
 }  // namespace
 
-// Timed launches of the chains into the per-CTA sink `out` (blocks slots).
-static cudaError_t run_probe(int dtype, int64_t iters, int blocks, void* out, double* flops_per_s,
-                             cudaStream_t s) {
+// Thread 0's chain sum, computed on the host with the same IEEE fused
+// multiply-adds and the same order of additions as the kernels (FE_F64,
+// FE_F32, or 3 for the packed FP32x2 chains, whose two halves start at c and
+// -c).  Used to check what the kernels stored in the sink.
+static double chain_sum_thread0(int dtype, int64_t iters) {
+    if (dtype == FE_F64) {
+        double x[8];
+        for (int c = 0; c < 8; ++c) x[c] = double(c);
+        for (int64_t i = 0; i < iters * 16; ++i)
+            for (int c = 0; c < 8; ++c) x[c] = std::fma(x[c], 0.999999, 1e-7);
+        return ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+    }
+    if (dtype == 3) {
+        float a[8], b[8];
+        for (int c = 0; c < 8; ++c) { a[c] = float(c); b[c] = float(-c); }
+        for (int64_t i = 0; i < iters * 8; ++i)
+            for (int c = 0; c < 8; ++c) {
+                a[c] = std::fma(a[c], 0.999999f, 1e-7f);
+                b[c] = std::fma(b[c], 0.999999f, 1e-7f);
+            }
+        float s = 0.f;
+        for (int c = 0; c < 8; ++c) s += a[c] + b[c];
+        return s;
+    }
+    float x[8];
+    for (int c = 0; c < 8; ++c) x[c] = float(c);
+    for (int64_t i = 0; i < iters * 16; ++i)
+        for (int c = 0; c < 8; ++c) x[c] = std::fma(x[c], 0.999999f, 1e-7f);
+    return ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+}
+
+// Reads slot `slot` of the sink (FP64 slots for FE_F64, FP32 otherwise) into
+// *v: through the pointer, or, when `sym` is set, through the symbol of the
+// static sink (so that a wrong device address of the array would show).
+static cudaError_t read_slot(int dtype, const void* out, bool sym, int slot, double* v, cudaStream_t s);
+
+// Timed launches of the chains into the per-CTA sink `out` (blocks slots),
+// then a check of the first and last slot against the host's chain sum.
+static cudaError_t run_probe(int dtype, int64_t iters, int blocks, void* out, bool sym, double* flops_per_s,
+                             cudaStream_t s, bool* sink_ok) {
     const int threads = 256;
-    cudaError_t e = cudaSuccess;
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
-    for (int rep = 0; rep < 2; ++rep) {   // first pass warms up the clocks
-        cudaEventRecord(t0, s);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e != cudaSuccess) {
+        if (t0) cudaEventDestroy(t0);
+        return e;
+    }
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // first pass warms up the clocks
+        e = cudaEventRecord(t0, s);
+        if (e != cudaSuccess) break;
         if (dtype == FE_F64)
             fma_chains<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.999999, 1e-7);
         else if (dtype == 3)
             fma2_chains<<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-7f);
         else
             fma_chains<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-7f);
-        cudaEventRecord(t1, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(t1, s);
     }
-    e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (e != cudaSuccess) return e;
     const double flops = 2.0 * 8 * 16 * (double)iters * blocks * threads;
     *flops_per_s = flops / (ms * 1e-3);
-    return cudaGetLastError();
+    // the sink: first and last CTA slot hold thread 0's chain sum
+    double first = 0.0, last = 0.0;
+    e = read_slot(dtype, out, sym, 0, &first, s);
+    if (e == cudaSuccess) e = read_slot(dtype, out, sym, blocks - 1, &last, s);
+    if (e != cudaSuccess) return e;
+    const double want = chain_sum_thread0(dtype, iters);
+    *sink_ok = first == want && last == want;
+    return cudaSuccess;
 }
 
 static cudaError_t probe_blocks(int& blocks) {
@@ -92,14 +146,15 @@ static cudaError_t probe_blocks(int& blocks) {
     return cudaSuccess;
 }
 
-cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s) {
+cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_t s, bool* sink_ok) {
     int blocks = 0;
     cudaError_t e = probe_blocks(blocks);
     if (e != cudaSuccess) return e;
     void* out = nullptr;
     e = cudaMallocAsync(&out, sizeof(double) * blocks, s);
     if (e != cudaSuccess) return e;
-    e = run_probe(dtype, iters, blocks, out, flops_per_s, s);
+    *sink_ok = false;
+    e = run_probe(dtype, iters, blocks, out, false, flops_per_s, s, sink_ok);
     const cudaError_t ef = cudaFreeAsync(out, s);
     return e != cudaSuccess ? e : ef;
 }
@@ -154,7 +209,29 @@ cudaError_t probe_fma_static(int dtype, int64_t iters, double* flops_per_s, cuda
         }
         out = g_sink_ptr[dev];
     }
-    return run_probe(dtype, iters, blocks, out, flops_per_s, s);
+    bool ok = false;
+    e = run_probe(dtype, iters, blocks, out, true, flops_per_s, s, &ok);
+    if (e == cudaSuccess && !ok) *too_many = -2;
+    return e;
+}
+
+static cudaError_t read_slot(int dtype, const void* out, bool sym, int slot, double* v, cudaStream_t s) {
+    const size_t elem = dtype == FE_F64 ? sizeof(double) : sizeof(float);
+    unsigned char buf[8] = {0};
+    cudaError_t e = sym ? cudaMemcpyFromSymbolAsync(buf, g_probe_sink, elem, elem * (size_t)slot,
+                                                     cudaMemcpyDeviceToHost, s)
+                        : cudaMemcpyAsync(buf, static_cast<const unsigned char*>(out) + elem * (size_t)slot, elem,
+                                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (elem == sizeof(double)) {
+        std::memcpy(v, buf, sizeof(double));
+    } else {
+        float f;
+        std::memcpy(&f, buf, sizeof(float));
+        *v = f;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace femf

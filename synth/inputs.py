@@ -115,6 +115,20 @@ CONFIGS: dict[str, Config] = {
     "free_p4": _cfg(name="free_p4", nx=4, ny=4, nz=2, hx=2.0, hy=2.0, hz=2.0, p=4,
                     n_orb=21, n_col_blocks=3, radius=3.0, env_s2=(3.0 / 1.75) ** 2,
                     n_wells=4, well_depth=1.0, well_sigma=1.0, dirichlet=0, index=14),
+    # Wide unions at small size: supports large against the box, so that runs
+    # of consecutive row blocks hold well over 128 columns between them
+    # (several 128-column output tiles of the Gram per group, mirrored
+    # off-diagonal tiles, row splits), at sizes the oracle checks in full.
+    "multi_p2": _cfg(name="multi_p2", nx=12, ny=8, nz=8, hx=1.0, hy=1.0, hz=1.0, p=2,
+                     n_orb=200, n_col_blocks=24, radius=3.4, env_s2=(3.4 / 1.75) ** 2,
+                     n_wells=6, well_depth=1.0, well_sigma=1.5, index=15),
+    "multi_p4": _cfg(name="multi_p4", nx=6, ny=4, nz=4, hx=2.0, hy=2.0, hz=2.0, p=4,
+                     n_orb=200, n_col_blocks=24, radius=3.4, env_s2=(3.4 / 1.75) ** 2,
+                     n_wells=6, well_depth=1.0, well_sigma=1.5, index=16),
+    # 16-wide column blocks whose unions exceed 256 columns.
+    "multi_w16_p2": _cfg(name="multi_w16_p2", nx=10, ny=8, nz=6, hx=1.0, hy=1.0, hz=1.0, p=2,
+                         n_orb=320, n_col_blocks=20, radius=4.0, env_s2=(4.0 / 1.75) ** 2,
+                         n_wells=4, well_depth=1.0, well_sigma=1.5, index=17),
     # Paper scale, p=2: 64x40x40 unit Q2 cells = 102,400 cells, 846,369 DoFs,
     # 12,800 row blocks; 320 orbitals in 38 column blocks; ~20% block fill;
     # 50 wells of depth 1 and width 2 cells.

@@ -5,8 +5,9 @@ through the same fe_apply_H_gram call the benchmark times.
 The oracle cannot assemble and apply the whole operator quickly at this
 size, so Y is checked on sampled rows (each computed one by one from the
 cells around the node), P^T P against the oracle's full FP64 product, and
-P^T Y on sampled column blocks, whose columns of Y the oracle computes from
-the rows of the pattern only.  Tolerances are the normwise bounds of the
+P^T Y on four or more column blocks (among them both ends of the widest
+union of a Gram work group), whose columns of Y the oracle computes from the
+rows of the pattern only.  Tolerances are the normwise bounds of the
 small-size tests, with the maximum taken over the checked entries.
 """
 import numpy as np
@@ -43,8 +44,28 @@ def _oracle_inputs(cfg, fp32):
     return mesh, blk, perm, ptr, mv, pat, cb_of_orb
 
 
-@pytest.mark.parametrize("name,dtype", [("p2", 1), ("p2", 2), ("p4", 1), ("p4", 2), ("large_p2", 1), ("large_p4", 1)],
-                         ids=["p2-f32", "p2-f64", "p4-f32", "p4-f64", "large_p2-f32", "large_p4-f32"])
+CASES = [("p2", 1), ("p2", 2), ("p4", 1), ("p4", 2), ("large_p2", 1), ("large_p2", 2), ("large_p4", 1),
+         ("large_p4", 2)]
+
+
+def _pty_blocks(pb, rng, n=4):
+    """Column blocks whose P^T Y columns are checked: those at both ends of the
+    widest union of 8 consecutive row blocks (the Gram's work groups), the
+    column block stored in the most row blocks, and random ones up to n."""
+    w = np.diff(pb.cbp)
+    best, uni = -1, None
+    for r0 in range(0, pb.mesh.n_row_blocks, 8):
+        u = np.unique(pb.col_idx[pb.row_ptr[r0]:pb.row_ptr[min(r0 + 8, pb.mesh.n_row_blocks)]])
+        if len(u) and w[u].sum() > best:
+            best, uni = w[u].sum(), u
+    counts = np.bincount(pb.col_idx, minlength=len(w))
+    pick = [int(uni[0]), int(uni[-1]), int(np.argmax(counts))]
+    rest = [c for c in range(len(w)) if c not in pick]
+    pick += [int(c) for c in rng.choice(rest, max(0, n - len(set(pick))), replace=False)]
+    return sorted(set(pick))
+
+
+@pytest.mark.parametrize("name,dtype", CASES, ids=[f"{n}-f{32 if d == 1 else 64}" for n, d in CASES])
 def test_paper_scale(name, dtype):
     cfg = inputs.get_config(name)
     fp32 = dtype == 1
@@ -91,7 +112,7 @@ def test_paper_scale(name, dtype):
     assert err <= tol["Y"], err
 
     # ---- P^T Y on sampled column blocks --------------------------------------
-    for c in rng.choice(len(ptr) - 1, 1, replace=False):
+    for c in _pty_blocks(pb, rng):
         rows = np.nonzero(pat[:, c])[0]
         rkeys = np.nonzero(np.isin(blk.owner_rank(np.arange(mesh.n_nodes)), rows))[0]
         cells = O.mesh_cells_touching(mesh, rkeys)

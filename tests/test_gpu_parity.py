@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {2: dict(Y=1e-12, PY=1e-12, PP=1e-12), 1: dict(Y=1e-5, PY=1e-6, PP=1e-10)}
 SMALL = ["tiny", "tiny_p4", "small_p1", "small_p2", "small_p3", "small_p4", "wide_p2",
-         "narrow_p2", "narrow_p4", "free_p2", "free_p4"]
+         "narrow_p2", "narrow_p4", "free_p2", "free_p4", "multi_p2", "multi_p4", "multi_w16_p2"]
 
 
 def _run_gpu(cfg, dtype):

@@ -1,10 +1,17 @@
 """The allocation-free ALU probe (fe_probe_fma_static) against the probe
 that allocates its sink (fe_probe_fma), through the C ABI.
 
-Both run the same FMA-chain kernels, so on the same device they must report
-the same throughput within the run-to-run spread of a timed kernel; the
-calls alternate twice so that the shared static sink is used by two calls
-in a row.  Kept in a file of its own, collected last."""
+Some callers cannot allocate device memory when they want the measurement,
+for instance a server that has already promised its whole memory budget to
+admitted requests; fe_probe_fma_static serves them from a fixed static
+array.  Both calls run the same FMA-chain kernels.  Each CTA stores thread
+0's chain sum in its slot, and each call reads slots back and compares them
+with the sum the host computes (the static variant through the array's
+symbol), returning FE_EDEVICE on a mismatch; so a call that succeeds has
+written and read the sink it was meant to use.  On the same device both must
+also report the same throughput within the run-to-run spread of a timed
+kernel.  The calls alternate twice, so the shared static sink serves two
+calls in a row.  Kept in a file of its own, collected last."""
 import ctypes as C
 
 import pytest
