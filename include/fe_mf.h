@@ -218,12 +218,22 @@ int fe_bcsr_bind(fe_bcsr* bcsr, void* values_dev, void* tables_dev, void* stream
  * ------------------------------------------------------------------------ */
 
 /* Y = mask(P) * (H P): Alg. 6 with the destination restricted to P's block
- * pattern.  Zeroes Y, then runs the matrix-free cell operator (gather of the
- * non-empty column blocks of each patch, sum-factorised values and gradients
- * at the Gauss points, quadrature of 1/2 grad.grad + V, integration, and
- * scatter-add into Y).  P and Y must have identical patterns and dtype
- * (FE_EPATTERN), P must be bound with tables and Y with values (FE_ESTATE),
- * the mesh uploaded and a potential of the same dtype registered (FE_ESTATE). */
+ * pattern.  Runs the matrix-free cell operator (gather of the non-empty
+ * column blocks of each patch, sum-factorised values and gradients at the
+ * Gauss points, quadrature of 1/2 grad.grad + V, integration) and writes the
+ * patch results into Y without atomics and without zeroing Y first: work
+ * items are taken in descending patch rank, and each row of Y is stored by
+ * the highest-ranked patch that contributes to it and then read, added to and
+ * stored back by the others in descending rank, each waiting (on the GPU,
+ * bounded in time) until its higher-ranked neighbour patches are done.  Every
+ * stored entry of Y is overwritten, and the result is the same bit for bit
+ * on every call.  The work counter and the per-patch completion counters live
+ * in P's table buffer and are reset by each call, so two calls with the same
+ * P (fe_apply_H, fe_apply_M, or the step calls) must not run concurrently.
+ * P and Y must have identical patterns and dtype (FE_EPATTERN), P must be
+ * bound with tables and Y with values (FE_ESTATE), the mesh uploaded and a
+ * potential of the same dtype registered (FE_ESTATE).  A wait that gives up
+ * sets the device status word (fe_mesh_check_device). */
 int fe_apply_H(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, void* stream);
 
 /* Y = mask(P) * (M P) with the mass matrix M_ij = sum_K int_K N_i N_j
@@ -311,11 +321,10 @@ int fe_trace_dot(const fe_bcsr* D, const fe_bcsr* G, double* out_dev, void* stre
  * ------------------------------------------------------------------------ */
 
 /* Launch knobs of fe_apply_H for source multivector P:
- *   persistent      0: one CTA per work unit (grid launch);
+ *   persistent      0: one CTA per work unit (grid launch); each CTA takes
+ *                      its unit from the work counter in P's table buffer;
  *                   1: persistent launch of ctas_per_sm CTAs per SM that take
- *                      units from a work counter stored in P's table buffer
- *                      (so two fe_apply_H calls with the same P must not run
- *                      concurrently on different streams);
+ *                      units from that counter until none is left;
  *   ctas_per_sm     1..32 (used by the persistent launch only);
  *   cells_per_round 0 = automatic, or 1, 2, 4, 8 = cap on the cells of the
  *                   patch a CTA holds at once (used by the p >= 3 kernel only).

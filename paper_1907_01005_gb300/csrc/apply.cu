@@ -6,7 +6,10 @@
 // (the patch's own row block and its seven lower neighbours, Alg. 4/5
 // semantics precomputed into the tile), runs the sum-factorised cell operator
 // on each of the patch's eight cells, accumulates the cell results into a
-// patch tensor in shared memory and scatter-adds the patch tensor into Y.
+// patch tensor in shared memory and writes the patch tensor into Y in the
+// conflict-free write of unit_common.cuh (tiles taken in descending patch
+// rank from a work counter; contributions to lower neighbours through halo
+// slots; every own row stored once; no zero-fill of Y, no global atomics).
 //
 // Thread mapping: a thread owns one (cell, column, plane) triple.  A cell
 // column is an n^3 tensor (n = p+1); its n threads each hold an n x n plane in
@@ -29,32 +32,6 @@ struct Geo {
     static constexpr int N3 = N * N * N;
 };
 
-// Row block slot and row index of patch-local node (i, j, k) of patch
-// (px, py, pz).  Along each axis: local index 0 of a patch that is not the
-// lowest belongs to the lower neighbour (where it is index 2p); a row block
-// of a patch at coordinate 0 also holds its index-0 nodes.
-template <int P>
-__device__ __forceinline__ void node_slot_row(int i, int j, int k, int px, int py, int pz,
-                                              int& slot, int& row) {
-    constexpr int Q = 2 * P;
-    int dx = (i == 0 && px > 0) ? 0 : 1;
-    int dy = (j == 0 && py > 0) ? 0 : 1;
-    int dz = (k == 0 && pz > 0) ? 0 : 1;
-    int ii = dx ? i : Q, jj = dy ? j : Q, kk = dz ? k : Q;
-    int qx = px - 1 + dx, qy = py - 1 + dy, qz = pz - 1 + dz;
-    int nxq = Q + (qx == 0), nyq = Q + (qy == 0);
-    int rx = ii - (qx == 0 ? 0 : 1), ry = jj - (qy == 0 ? 0 : 1), rz = kk - (qz == 0 ? 0 : 1);
-    slot = dx + 2 * dy + 4 * dz;
-    row = rx + nxq * (ry + nyq * rz);
-}
-
-__device__ __forceinline__ bool on_boundary(int I, int J, int K, int lx, int ly, int lz) {
-    return I == 0 || J == 0 || K == 0 || I == lx - 1 || J == ly - 1 || K == lz - 1;
-}
-
-__device__ __forceinline__ void atomic_add_shared(float* a, float v) { atomicAdd(a, v); }
-__device__ __forceinline__ void atomic_add_shared(double* a, double v) { atomicAdd(a, v); }
-
 // Threads per CTA are capped so that the per-thread planes (four n x n arrays)
 // stay in registers: 8 cells x 16 columns x n planes for p <= 2, half of that
 // for p >= 3.
@@ -74,26 +51,36 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
     T* exA = Yp + NPN * ldmax;                       // [cpr*wmax][N3] exchange
     T* exB = exA + cpr * wmax * N3;
 
-    const Tile& tile = a.tiles[blockIdx.x];
+    // tiles in descending order (descending patch rank, the order of the write)
+    __shared__ int64_t sTicket;
+    if (threadIdx.x == 0) sTicket = (int64_t)atomicAdd(a.ticket, 1ull);
+    __syncthreads();
+    if (sTicket >= a.n_tiles) return;
+    const Tile& tile = a.tiles[a.n_tiles - 1 - sTicket];
     const int w = tile.width, ld = tile.ld;
     const int px = tile.pxyz & 1023, py = (tile.pxyz >> 10) & 1023, pz = tile.pxyz >> 20;
     const int cellmask = tile.cellmask;
-    if (w > wmax || w < 1 || ld < w || ld > ldmax || ld % (16 / (int)sizeof(T)) != 0 ||
+    const bool in_mesh = px < a.npx && py < a.npy && pz < a.npz;
+    if (!in_mesh || w > wmax || w < 1 || ld < w || ld > ldmax || ld % (16 / (int)sizeof(T)) != 0 ||
         ldmax % (16 / (int)sizeof(T)) != 0) {
-        if (threadIdx.x == 0) atomicExch(a.status, kDevBadTile);
+        // a malformed tile: reported, skipped, and counted as finished so
+        // that its neighbours do not wait for it
+        if (threadIdx.x == 0) {
+            atomicExch(a.status, kDevBadTile);
+            if (in_mesh) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+        }
         return;
     }
     __shared__ int64_t sOff[8];
-    __shared__ int sNode[NPN];                       // (slot << 16) | row, or -1 (boundary / absent block)
-    if (threadIdx.x < 8) sOff[threadIdx.x] = tile.off[threadIdx.x];
-    __syncthreads();
-    for (int n = threadIdx.x; n < NPN; n += blockDim.x) {
-        const int i = n % NP, j = (n / NP) % NP, k = n / (NP * NP);
-        int slot, row;
-        node_slot_row<P>(i, j, k, px, py, pz, slot, row);
-        const bool bnd = a.dirichlet && on_boundary(2 * P * px + i, 2 * P * py + j, 2 * P * pz + k, a.lx, a.ly, a.lz);
-        sNode[n] = (bnd || sOff[slot] < 0) ? -1 : ((slot << 16) | row);
+    __shared__ int32_t sHout[8], sHin[8];
+    __shared__ int sNode[NPN];                       // node_entry: row, owner slot, boundary bit, face data
+    if (threadIdx.x < 8) {
+        sOff[threadIdx.x] = tile.off[threadIdx.x];
+        sHout[threadIdx.x] = tile.hout[threadIdx.x];
+        sHin[threadIdx.x] = tile.hin[threadIdx.x];
     }
+    for (int n = threadIdx.x; n < NPN; n += blockDim.x)
+        sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet, a.npx, a.npy, a.npz);
     __syncthreads();
     constexpr int CH = 16 / sizeof(T);               // elements per 16-byte chunk (ld is a multiple)
 
@@ -103,8 +90,9 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
         const unsigned ubase = (unsigned)__cvta_generic_to_shared(U);
         for (int node = threadIdx.x; node < NPN; node += blockDim.x) {
             const int ne = sNode[node];
-            const bool ok = ne >= 0;
-            const T* src = ok ? a.P + sOff[ne >> 16] + (int64_t)(ne & 0xffff) * ld : a.P;
+            const int64_t o = (ne & kBoundary) ? -1 : sOff[(ne >> 16) & 7];
+            const bool ok = o >= 0;
+            const T* src = ok ? a.P + o + (int64_t)(ne & 0xffff) * ld : a.P;
             const unsigned dst = ubase + (unsigned)(node * ld * sizeof(T));
             for (int c0 = 0; c0 < ld; c0 += CH)
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + c0 * (int)sizeof(T)),
@@ -270,33 +258,52 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
                     T s = T(0);
 #pragma unroll
                     for (int kq = 0; kq < N; ++kq) s = fma(K.Sb[ka][kq], pb[kq][ia], s);
-                    const int node = (cx * P + ia) + NP * ((cy * P + t) + NP * (cz * P + ka));
-                    atomic_add_shared(&Yp[node * ld + col], s);
+                    pa[ka][ia] = s;
                 }
         }
-        __syncthreads();
+        // add the cells' results into the patch tensor one cell slot at a
+        // time (cells share face, edge and centre nodes): a fixed order of
+        // the additions, and no two threads of a phase touch the same node
+        for (int k = 0; k < cpr; ++k) {
+            if (act && cslot == k) {
+#pragma unroll
+                for (int ka = 0; ka < N; ++ka)
+#pragma unroll
+                    for (int ia = 0; ia < N; ++ia) {
+                        const int node = (cx * P + ia) + NP * ((cy * P + t) + NP * (cz * P + ka));
+                        Yp[node * ld + col] += pa[ka][ia];
+                    }
+            }
+            __syncthreads();
+        }
     }
 
-    // ---- scatter-add (Alg. 6, write step): 16-byte vector reductions, one
-    // task per node row ---------------------------------------------------------
+    // ---- write into Y (Alg. 6, write step; unit_common.cuh), one task per
+    // node row: (1) contributions to the lower neighbours' rows into their
+    // halo slots, (2) wait for the upper neighbours' halos, (3) own rows --------
+    constexpr int kElem16 = 16 / sizeof(T);
     for (int node = threadIdx.x; node < NPN; node += blockDim.x) {
         const int ne = sNode[node];
-        if (ne < 0) continue;
-        const T* ys = Yp + node * ld;
-        T* yd = a.Y + sOff[ne >> 16] + (int64_t)(ne & 0xffff) * ld;
-        for (int c0 = 0; c0 < ld; c0 += CH) {
-            T v[CH];
-            if constexpr (CH == 4) {
-                const float4 f = *reinterpret_cast<const float4*>(ys + c0);
-                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-            } else {
-                const double2 f = *reinterpret_cast<const double2*>(ys + c0);
-                v[0] = f.x; v[1] = f.y;
-            }
-            bool nz = false;
-#pragma unroll
-            for (int h = 0; h < CH; ++h) nz |= v[h] != T(0);   // padding columns stay zero
-            if (nz) red_chunk(yd + c0, v);
+        const int slot = (ne >> 16) & 7;
+        if (slot == 7 || (ne & kBoundary)) continue;
+        const int32_t h = sHout[slot];
+        if (h < 0) continue;
+        put_halo_row(a.halo + (int64_t)h * kElem16 + (ne >> kAuxShift) * ld, Yp + node * ld, ld);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+    if (threadIdx.x < 32 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) &&
+        threadIdx.x == 0)
+        atomicExch(a.status, kDevTimeout);
+    __syncthreads();
+    const int64_t oown = sOff[7];
+    if (oown >= 0) {
+        for (int node = threadIdx.x; node < NPN; node += blockDim.x) {
+            const int ne = sNode[node];
+            if (((ne >> 16) & 7) != 7) continue;
+            const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
+            put_own_row<P>(a.Y + oown + (int64_t)(ne & 0xffff) * ld, Yp + node * ld, ld, (ne & kBoundary) != 0,
+                           (ne >> kAuxShift) & 7, a.halo, sHin, i, j, k, px, py, pz);
         }
     }
 }

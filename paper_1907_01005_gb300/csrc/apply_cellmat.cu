@@ -23,10 +23,13 @@
 // which leaves an error of about 2^-21 relative per product.
 //
 // Data movement is that of the register kernel: 16-byte cp.async gather of the
-// patch tensor (node rows of kUnitLdSum with the unit's blocks side by side), shared-memory atomics of the cells' results into a zeroed
-// patch tensor (here it reuses the gather buffer), 16-byte vector reductions
-// into Y.  The constant operand tiles (both parts of K_L, S3, Sb3) are copied
-// once per CTA; CTAs are persistent and take units from a work counter.
+// patch tensor (node rows of kUnitLdSum with the unit's blocks side by side),
+// the cells' results summed into a zeroed patch tensor in a fixed order
+// (merge_cells_store; here the tensor reuses the gather buffer and the
+// exchange uses the free A tiles), and the conflict-free write into Y of
+// unit_common.cuh (units in descending patch rank, halo slots).  The constant operand
+// tiles (both parts of K_L, S3, Sb3) are copied once per CTA; CTAs are
+// persistent and take units from a work counter.
 #include <algorithm>
 #include <cstdint>
 
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
     unsigned char* sm = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
     float* U = reinterpret_cast<float*>(sm + G::OFF_U);    // gathered patch tensor, then the cells' results
     float* Vs = reinterpret_cast<float*>(sm + G::OFF_V);   // [8][N3]
-    __shared__ int32_t sOff[kUnitBlocks][8];
+    __shared__ int32_t sOff[kUnitBlocks][8], sHout[kUnitBlocks][8], sHin[kUnitBlocks][8];
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
     __shared__ int sNode[NPN];
     __shared__ int64_t sItem;
@@ -244,12 +247,14 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
     const int cell = tid / L, lane = tid % L;
     const int cx = cell & 1, cy = (cell >> 1) & 1, cz = (cell >> 2) & 1;
 
-    if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);
+    if (tid == 0) sItem = (int64_t)atomicAdd(a.ticket, 1ull);
     __syncthreads();
-    int64_t item = sItem;
-    while (item < a.n_units) {
-        const Unit& unit = a.units[item];
+    int64_t ticket = sItem;
+    while (ticket < a.n_units) {
+        // units in descending order: descending patch rank, the order of the write
+        const Unit& unit = a.units[a.n_units - 1 - ticket];
         const int px = unit.pxyz & 1023, py = (unit.pxyz >> 10) & 1023, pz = unit.pxyz >> 20;
+        const bool in_mesh = px < a.npx && py < a.npy && pz < a.npz;
         // work-list check, as in the register kernel
         bool unit_ok = unit.nb >= 1 && unit.nb <= kUnitBlocks;
         if (unit_ok) {
@@ -262,6 +267,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
             }
             unit_ok = unit_ok && lds <= kUnitLdSum && lanes <= L;
         }
+        unit_ok = unit_ok && in_mesh;
         if (!unit_ok && tid == 0) atomicExch(a.status, kDevBadTile);
         if (unit_ok) {
             // ---- unit tables ------------------------------------------------
@@ -274,7 +280,10 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                 }
                 sLaneB[tid] = b;
                 sLaneA[tid] = col;
-                sOff[tid >> 3][tid & 7] = (tid >> 3) < unit.nb ? unit.off[tid >> 3][tid & 7] : -1;
+                const bool has = (tid >> 3) < unit.nb;
+                sOff[tid >> 3][tid & 7] = has ? unit.off[tid >> 3][tid & 7] : -1;
+                sHout[tid >> 3][tid & 7] = has ? unit.hout[tid >> 3][tid & 7] : -1;
+                sHin[tid >> 3][tid & 7] = has ? unit.hin[tid >> 3][tid & 7] : -1;
             }
             if (tid == 0) {
                 int base = 0;
@@ -286,7 +295,8 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                     base += ldq;
                 }
             }
-            for (int n = tid; n < NPN; n += blockDim.x) sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
+            for (int n = tid; n < NPN; n += blockDim.x)
+                sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet, a.npx, a.npy, a.npz);
             __syncthreads();
 
             static_assert(kUnitBlocks == 4, "task index: node << 2 | block");
@@ -300,7 +310,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                     if (b >= nb) continue;
                     const int ld = sLd[b];
                     const int ne = sNode[node];
-                    const int32_t o = ne >= 0 ? sOff[b][ne >> 16] : -1;
+                    const int32_t o = (ne & kBoundary) ? -1 : sOff[b][(ne >> 16) & 7];
                     const bool ok = o >= 0;
                     const float* src = ok ? a.P + (int64_t)o * 4 + (ne & 0xffff) * ld : a.P;
                     const unsigned dst = ubase + (unsigned)((node * S + sBase[b]) * 4);
@@ -323,7 +333,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
             // ---- stage 1 operand: the thread's cell-column at its cell's nodes
             const int b = sLaneB[lane];
             const bool act = b >= 0 && ((sMask[b] >> cell) & 1);
-            const int base = act ? sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * S : 0;
+            const int base = b >= 0 ? sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * S : 0;
             {
                 float x[4 * KCH];
 #pragma unroll
@@ -364,7 +374,10 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
             if (tid == 0 && !mbar_wait(bar, phase, kWaitLimitNs)) sFail = 1;
             phase ^= 1;
             __syncthreads();
-            if (sFail) break;
+            if (sFail) {                                  // count the unit as finished: no neighbour waits on it
+                if (tid == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+                break;
+            }
             tc_fence_after();
 
             if constexpr (!MASS) {
@@ -398,49 +411,70 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                 }
                 phase ^= 1;
                 __syncthreads();
-                if (sFail) break;
+                if (sFail) {
+                    if (tid == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+                    break;
+                }
                 tc_fence_after();
             }
 
             // ---- the cell's result into the patch tensor ---------------------
+            // (shared nodes summed in a fixed order through the free A tiles,
+            // each node stored once)
             {
                 float y[NPAD];
                 tmem_load<NPAD>(tD, y);
-                if (act) {
+                float tcell[N][N][N];
 #pragma unroll
-                    for (int z = 0; z < N; ++z)
+                for (int z = 0; z < N; ++z)
 #pragma unroll
-                        for (int yy = 0; yy < N; ++yy)
+                    for (int yy = 0; yy < N; ++yy)
 #pragma unroll
-                            for (int xx = 0; xx < N; ++xx)
-                                atomicAdd(&U[base + ((z * NP + yy) * NP + xx) * S], y[(z * N + yy) * N + xx]);
-                }
+                        for (int xx = 0; xx < N; ++xx) tcell[z][yy][xx] = act ? y[(z * N + yy) * N + xx] : 0.f;
+                static_assert(2 * kMergeFace<P> * 4 <= 4 * G::TILE, "exchange buffer in the A tiles");
+                merge_cells_store<P, S, NP, false>(tcell, cell, lane, sLaneB[lane] >= 0,
+                                                   reinterpret_cast<float*>(sm + G::OFF_AH), U, base);
             }
             tc_fence_before();
             __syncthreads();
 
-            // ---- scatter-add of 16-byte chunks, one task per (node, block) row -
+            // ---- write into Y (unit_common.cuh), one task per (node, block) row
             for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
                 const int node = e >> 2, bb = e & 3;
                 if (bb >= nb) continue;
                 const int ne = sNode[node];
-                if (ne < 0) continue;
-                const int32_t o = sOff[bb][ne >> 16];
+                const int slot = (ne >> 16) & 7;
+                if (slot == 7 || (ne & kBoundary)) continue;
+                const int32_t h = sHout[bb][slot];
+                if (h < 0) continue;
+                const int ldb = sLd[bb];
+                put_halo_row(a.halo + (int64_t)h * 4 + (ne >> kAuxShift) * ldb, U + node * S + sBase[bb], ldb);
+            }
+            __syncthreads();
+            if (tid == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+            if (warp == 0 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) && tid == 0)
+                atomicExch(a.status, kDevTimeout);
+            __syncthreads();
+            for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
+                const int node = e >> 2, bb = e & 3;
+                if (bb >= nb) continue;
+                const int ne = sNode[node];
+                if (((ne >> 16) & 7) != 7) continue;
+                const int32_t o = sOff[bb][7];
                 if (o < 0) continue;
                 const int ldb = sLd[bb];
-                const float* ys = U + node * S + sBase[bb];
-                float* yd = a.Y + (int64_t)o * 4 + (ne & 0xffff) * ldb;
-                for (int c0 = 0; c0 < ldb; c0 += CH) {
-                    const float4 f = *reinterpret_cast<const float4*>(ys + c0);
-                    const float v[4] = {f.x, f.y, f.z, f.w};
-                    if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f) red_chunk(yd + c0, v);
-                }
+                const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
+                put_own_row<P>(a.Y + (int64_t)o * 4 + (ne & 0xffff) * ldb, U + node * S + sBase[bb], ldb,
+                               (ne & kBoundary) != 0, (ne >> kAuxShift) & 7, a.halo, sHin[bb], i, j, k, px, py, pz);
             }
         }  // unit_ok
-        __syncthreads();                                  // shared tables are rebuilt for the next unit
-        if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);
+        else if (tid == 0 && in_mesh) {
+            mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it
+        }
+        __syncthreads();                                  // rows written; shared tables are rebuilt for the next unit
+        if (tid == 0) sItem = (int64_t)atomicAdd(a.ticket, 1ull);
         __syncthreads();
-        item = sItem;
+        ticket = sItem;
     }
 
     // ---- teardown: on a time-out, give the MMAs in flight one more bounded

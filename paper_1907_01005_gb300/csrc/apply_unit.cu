@@ -13,11 +13,12 @@
 // fill for absent blocks and boundary nodes) into a patch tensor
 // U[node][kUnitLdSum] whose rows hold the unit's blocks side by side (the 32
 // lanes of a warp then read one row: no bank conflicts between blocks, and
-// the row stride is a compile-time constant); the
-// cells add their results into a matching zeroed tensor with shared-memory
-// atomics; the scatter adds 16-byte chunks into Y
-// with vector reductions (red.global.add.v4.f32), 4x fewer than scalar
-// atomics.
+// the row stride is a compile-time constant); the cells' results are summed
+// into a matching zeroed tensor in a fixed order (merge_cells_store, no
+// shared-memory atomics); the tensor goes
+// into Y in the ordered, conflict-free write of unit_common.cuh (units in
+// descending patch rank, first writer stores, later contributors add), so Y
+// needs no zero-fill and no global atomics are used.
 #include <algorithm>
 
 #include "fe_internal.h"
@@ -33,8 +34,11 @@ struct UnitGeo {
     static constexpr int THREADS = 8 * L;
     static constexpr int CH = 16 / sizeof(T);          // elements per 16-byte chunk
     static constexpr int TEN = NPN * kUnitLdSum;       // elements of one patch tensor (all blocks)
+    // the region of U also holds the exchange buffer of the cell merge
+    static constexpr int UEX = TEN > 2 * kMergeFace<P> ? TEN : 2 * kMergeFace<P>;
     // gathered input U, accumulated output Yp, V at the Gauss points
-    static constexpr size_t bytes = (size_t)(2 * TEN + 8 * N3) * sizeof(T);
+    static constexpr size_t bytes = (size_t)(UEX + TEN + 8 * N3) * sizeof(T);
+    static_assert(UEX * sizeof(T) % 16 == 0, "the patch tensors start on 16-byte boundaries");
 };
 
 // resident CTAs per SM the register budget must allow (a cell-column's
@@ -50,23 +54,22 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     constexpr int CH = G::CH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* U = reinterpret_cast<T*>(smem_raw);         // [NPN][kUnitLdSum]: block b at columns sBase[b] ..
-    T* Yp = U + G::TEN;                            // same layout, accumulated cell results
+    T* Yp = U + G::UEX;                            // same layout, accumulated cell results
     T* Vs = Yp + G::TEN;                           // [8][N3]  V at the Gauss points
-    __shared__ int32_t sOff[kUnitBlocks][8];
+    __shared__ int32_t sOff[kUnitBlocks][8], sHout[kUnitBlocks][8], sHin[kUnitBlocks][8];
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
-    __shared__ int sNode[NPN];                     // (slot << 16) | row, or -1 on the boundary
+    __shared__ int sNode[NPN];                     // node_entry: row, owner slot, first-writer and boundary bits
     __shared__ int64_t sItem;
     const int tid = threadIdx.x;
     constexpr int kElem16 = 16 / sizeof(T);        // elements per 16-byte offset unit
-    // One unit per CTA, or (persistent launch) units pulled from a ticket
-    // counter until the list is exhausted.
-    int64_t item = blockIdx.x;
-    if (a.ticket) {
-        if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);
-        __syncthreads();
-        item = sItem;
-    }
-    while (item < a.n_units) {
+    // Units are taken from a work counter in descending order (descending
+    // patch rank, the order of the write): one per CTA, or (persistent
+    // launch) until the list is exhausted.
+    if (tid == 0) sItem = (int64_t)atomicAdd(a.ticket, 1ull);
+    __syncthreads();
+    int64_t ticket = sItem;
+    while (ticket < a.n_units) {
+    const int64_t item = a.n_units - 1 - ticket;
     const Unit& unit = a.units[item];
     const int px = unit.pxyz & 1023, py = (unit.pxyz >> 10) & 1023, pz = unit.pxyz >> 20;
     // Work-list check: the host packs 1..kUnitBlocks blocks with 1 <= width <= ld,
@@ -84,6 +87,8 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         }
         unit_ok = unit_ok && lds <= kUnitLdSum && lanes <= L;
     }
+    const bool in_mesh = px < a.npx && py < a.npy && pz < a.npz;
+    unit_ok = unit_ok && in_mesh;
     if (!unit_ok && tid == 0) atomicExch(a.status, kDevBadTile);
     if (unit_ok) {
 
@@ -97,7 +102,10 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         }
         sLaneB[tid] = b;
         sLaneA[tid] = col;
-        sOff[tid >> 3][tid & 7] = (tid >> 3) < unit.nb ? unit.off[tid >> 3][tid & 7] : -1;
+        const bool has = (tid >> 3) < unit.nb;
+        sOff[tid >> 3][tid & 7] = has ? unit.off[tid >> 3][tid & 7] : -1;
+        sHout[tid >> 3][tid & 7] = has ? unit.hout[tid >> 3][tid & 7] : -1;
+        sHin[tid >> 3][tid & 7] = has ? unit.hin[tid >> 3][tid & 7] : -1;
     }
     if (tid == 0) {
         int base = 0;
@@ -109,7 +117,8 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
             base += ldq;
         }
     }
-    for (int n = tid; n < NPN; n += blockDim.x) sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet);
+    for (int n = tid; n < NPN; n += blockDim.x)
+        sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet, a.npx, a.npy, a.npz);
     __syncthreads();
 
     static_assert(kUnitBlocks == 4, "task index: node << 2 | block");
@@ -125,7 +134,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
             if (b >= nb) continue;
             const int ld = sLd[b];
             const int ne = sNode[node];
-            const int32_t o = ne >= 0 ? sOff[b][ne >> 16] : -1;
+            const int32_t o = (ne & kBoundary) ? -1 : sOff[b][(ne >> 16) & 7];
             const bool ok = o >= 0;
             const T* src = ok ? a.P + (int64_t)o * kElem16 + (ne & 0xffff) * ld : a.P;
             const unsigned dst = ubase + (unsigned)((node * S + sBase[b]) * sizeof(T));
@@ -154,16 +163,19 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         const int cx = cell & 1, cy = (cell >> 1) & 1, cz = (cell >> 2) & 1;
         const int b = sLaneB[lane];
         const bool act = b >= 0 && ((sMask[b] >> cell) & 1);
+        // element of local node (z, y, x) of this cell in both patch tensors
+        const int base = b >= 0 ? sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * S : 0;
+        T u[N][N][N], t[N][N][N];
         if (act) {
-            // element of local node (z, y, x) of this cell in both patch tensors
-            const int base = sBase[b] + sLaneA[lane] + ((cz * P * NP + cy * P) * NP + cx * P) * S;
-            T u[N][N][N], t[N][N][N];
 #pragma unroll
             for (int z = 0; z < N; ++z)
 #pragma unroll
                 for (int y = 0; y < N; ++y)
 #pragma unroll
                     for (int x = 0; x < N; ++x) u[z][y][x] = U[base + ((z * NP + y) * NP + x) * S];
+        }
+        __syncthreads();                               // U is read: it becomes the merge's exchange buffer
+        if (act) {
             const auto& K = a.k;
             // Sweeps run coefficient-outer: each coefficient is applied to all
             // N^2 lines of the sweep.
@@ -211,50 +223,62 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
             SWEEP(K.Sb, u[m][q][n], t[m][p2][n])
             SWEEP(K.Sb, t[q][m][n], u[p2][m][n])
 #undef SWEEP
-            // add the cell's result into the patch tensor (nodes on faces,
-            // edges and the centre are shared with the neighbouring cells)
+        } else {
 #pragma unroll
             for (int z = 0; z < N; ++z)
 #pragma unroll
                 for (int y = 0; y < N; ++y)
 #pragma unroll
-                    for (int x = 0; x < N; ++x) atomicAdd(&Yp[base + ((z * NP + y) * NP + x) * S], t[z][y][x]);
+                    for (int x = 0; x < N; ++x) t[z][y][x] = T(0);
         }
+        // the cells' results into the patch tensor: nodes on faces, edges and
+        // the centre are shared with the neighbouring cells and are summed in
+        // a fixed order, each node stored once
+        merge_cells_store<P, S, NP, false>(t, cell, lane, b >= 0, U, Yp, base);
     }
     __syncthreads();
 
-    // ---- scatter-add of 16-byte chunks (Alg. 6, write step) -----------------
+    // ---- write into Y (Alg. 6, write step; unit_common.cuh) ------------------
+    // (1) contributions to the lower neighbours' rows into their halo slots
     for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
         const int node = e >> 2, b = e & 3;
         if (b >= nb) continue;
         const int ne = sNode[node];
-        if (ne < 0) continue;
-        const int32_t o = sOff[b][ne >> 16];
+        const int slot = (ne >> 16) & 7;
+        if (slot == 7 || (ne & kBoundary)) continue;
+        const int32_t h = sHout[b][slot];
+        if (h < 0) continue;
+        const int ld = sLd[b];
+        put_halo_row(a.halo + (int64_t)h * kElem16 + (ne >> kAuxShift) * ld, Yp + node * S + sBase[b], ld);
+    }
+    __syncthreads();
+    if (tid == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+    // (2) the upper neighbours' halos addressed to this patch
+    if (tid < 32 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) && tid == 0)
+        atomicExch(a.status, kDevTimeout);
+    __syncthreads();
+    // (3) own rows: own part plus the halo rows, stored once
+    for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
+        const int node = e >> 2, b = e & 3;
+        if (b >= nb) continue;
+        const int ne = sNode[node];
+        if (((ne >> 16) & 7) != 7) continue;
+        const int32_t o = sOff[b][7];
         if (o < 0) continue;
         const int ld = sLd[b];
-        const T* ys = Yp + node * S + sBase[b];
-        T* yd = a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld;
-        for (int c0 = 0; c0 < ld; c0 += CH) {
-            T v[CH];
-            if constexpr (CH == 4) {
-                const float4 f = *reinterpret_cast<const float4*>(ys + c0);
-                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-            } else {
-                const double2 f = *reinterpret_cast<const double2*>(ys + c0);
-                v[0] = f.x; v[1] = f.y;
-            }
-            bool nz = false;
-#pragma unroll
-            for (int q = 0; q < CH; ++q) nz |= v[q] != T(0);
-            if (nz) red_chunk(yd + c0, v);
-        }
+        const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
+        put_own_row<P>(a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld, Yp + node * S + sBase[b], ld,
+                       (ne & kBoundary) != 0, (ne >> kAuxShift) & 7, a.halo, sHin[b], i, j, k, px, py, pz);
     }
     }  // unit_ok
-    if (!a.ticket) break;
-    __syncthreads();                                   // shared tables are rebuilt for the next unit
-    if (tid == 0) sItem = atomicAdd(a.ticket, 1ull);
+    else if (tid == 0 && in_mesh) {
+        mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it
+    }
+    __syncthreads();                                   // the unit's rows are written (shared tables free)
+    if (tid == 0 && a.persistent) sItem = (int64_t)atomicAdd(a.ticket, 1ull);
+    if (!a.persistent) break;
     __syncthreads();
-    item = sItem;
+    ticket = sItem;
     }
 }
 
@@ -279,7 +303,7 @@ cudaError_t launch_units_p(const ApplyUnitArgs<T>& a, cudaStream_t s) {
     }
     if (a.n_units == 0) return cudaSuccess;
     unsigned grid = (unsigned)a.n_units;
-    if (a.ticket) {
+    if (a.persistent) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

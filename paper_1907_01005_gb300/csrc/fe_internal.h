@@ -42,8 +42,17 @@ struct CellConsts {
 // names the row block of patch (px - 1 + dx, py - 1 + dy, pz - 1 + dz); off[b]
 // is the element offset of block (that row block, column block) in the value
 // array, or -1 when the block is not stored (or the patch does not exist).
+// Halo slots of the apply's write (unit_common.cuh): slot (block (r, c), e)
+// holds the contributions of patch r + e (e = ex + 2 ey + 4 ez != 0, an
+// upper neighbour of r) to the rows of block (r, c) on r's face with mask e,
+// as rows of the block's row stride, in the face order of halo_face_index.
+// hout[s] (s != 7): the slot this patch writes for the block of slot s;
+// hin[e]: the slots (own block, e) this patch reads.  Offsets in 16-byte
+// units from the start of the halo region, -1 where there is none.
 struct Tile {
     int64_t off[8];
+    int32_t hout[8];
+    int32_t hin[8];
     int32_t patch;      // rank of the patch (= its row block)
     int32_t pxyz;       // px | py << 10 | pz << 20
     int32_t width;      // column block width
@@ -61,6 +70,8 @@ constexpr int kUnitLanes = 32;
 constexpr int kUnitLdSum = 36;    // sum of the blocks' row strides in a unit
 struct Unit {
     int32_t off[kUnitBlocks][8];
+    int32_t hout[kUnitBlocks][8];   // halo slots written (see Tile), per block and slot
+    int32_t hin[kUnitBlocks][8];    // halo slots read, per block and upper-neighbour offset e
     int32_t patch;      // rank of the patch
     int32_t pxyz;       // px | py << 10 | pz << 20
     int32_t nb;         // column blocks in the unit
@@ -137,6 +148,10 @@ struct ApplyArgs {
     int32_t ldmax;            // largest row stride (a multiple of 16 bytes): row stride capacity of
                               // the patch tensors in shared memory
     int32_t cells_per_round;  // cells processed concurrently (1, 2, 4 or 8)
+    unsigned long long* ticket;   // work counter (zeroed before the launch): tiles go in descending order
+    int32_t* done;            // tiles per patch whose halo is written (zeroed before the launch), by patch id
+    const int32_t* count;     // tiles per patch, by patch id
+    T* halo;                  // halo region (Tile.hout / hin offsets)
     int32_t* status;          // device status word (0 = ok)
     int32_t mass;             // 1: the mass operator (no gradient term, V = 1; Vq unused)
     CellConsts<T> k;
@@ -167,8 +182,13 @@ struct ApplyUnitArgs {
     const T* Vq;
     const Unit* units;
     int64_t n_units;
-    unsigned long long* ticket;   // persistent launch: work counter (zeroed before launch), else null
-    int32_t ctas_per_sm;          // persistent launch: CTAs per SM
+    unsigned long long* ticket;   // work counter (zeroed before the launch): units go in descending order
+    int32_t persistent;           // 1: ctas_per_sm CTAs per SM loop over the work counter; 0: a CTA per unit
+    int32_t ctas_per_sm;
+    int32_t* done;                // units per patch whose halo is written (zeroed before the launch), by patch id
+    const int32_t* count;         // units per patch, indexed by patch id
+    T* halo;                      // halo region (Unit.hout / hin offsets)
+    int32_t npx, npy, npz;
     int32_t lx, ly, lz;
     int32_t dirichlet;
     int32_t* status;
@@ -195,6 +215,10 @@ struct CellMatArgs {
     const Unit* units;
     int64_t n_units;
     unsigned long long* ticket;   // work counter, zeroed before the launch (CTAs are persistent)
+    int32_t* done;                // units per patch whose halo is written (zeroed before the launch), by patch id
+    const int32_t* count;         // units per patch, by patch id
+    float* halo;                  // halo region (Unit.hout / hin offsets)
+    int32_t npx, npy, npz;
     int32_t lx, ly, lz;
     int32_t dirichlet;
     int32_t* status;

@@ -199,7 +199,15 @@ struct fe_bcsr {
     size_t off_ucol0 = 0, off_rbunion = 0, off_xround = 0;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
     size_t off_tcg = 0, off_tcpy = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
-    size_t off_units = 0, off_ld = 0, off_ticket = 0;
+    size_t off_units = 0, off_ld = 0, off_ticket = 0, sync_bytes = 0, off_ucnt = 0, off_tcnt = 0;
+    // work items of the apply per patch (by patch id px + npx (py + npy pz)):
+    // packed units (p <= 2 and the cell-matrix form) and tiles (p >= 3)
+    std::vector<int32_t> ucount, tcount;
+    // halo slots of the apply's write, [stored block][upper-neighbour offset e]
+    // in 16-byte units (-1: none), and the size of the halo region
+    std::vector<int32_t> hslot;
+    int64_t halo_elems = 0;
+    size_t off_halo = 0;
     // launch configuration of the apply (set by fe_bcsr_set_launch / fe_autotune)
     int32_t persistent = 0, ctas_per_sm = 4, cells_per_round = 0;
     int32_t closed = 0;   // the caller declares the pattern closed for P's values (fe_bcsr_set_closed)
@@ -722,6 +730,31 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->n_values = o;
         b->fingerprint = fp;
 
+        // ---- halo slots: block (r, c) gets one per upper neighbour r + e
+        // that exists, holding that neighbour's contributions to the rows of
+        // r's face with mask e (the free directions over r's own node range)
+        b->hslot.assign((size_t)nnz * 8, -1);
+        {
+            const int q = 2 * m->p;
+            int64_t h = 0;
+            for (int r = 0; r < R; ++r) {
+                int px, py, pz;
+                m->pxyz(m->rank_to_pid[r], px, py, pz);
+                const int n3[3] = {q + (px == 0), q + (py == 0), q + (pz == 0)};
+                const bool up[3] = {px + 1 < m->np[0], py + 1 < m->np[1], pz + 1 < m->np[2]};
+                for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k)
+                    for (int e = 1; e < 8; ++e) {
+                        const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+                        if ((ex && !up[0]) || (ey && !up[1]) || (ez && !up[2])) continue;
+                        const int64_t rows = (int64_t)(ex ? 1 : n3[0]) * (ey ? 1 : n3[1]) * (ez ? 1 : n3[2]);
+                        if (h * (int64_t)b->elem() / 16 >= (int64_t)INT32_MAX) throw std::bad_alloc();
+                        b->hslot[(size_t)k * 8 + e] = int32_t(h * (int64_t)b->elem() / 16);
+                        h += rows * b->ld[b->col_idx[k]];   // a multiple of 16 bytes
+                    }
+            }
+            b->halo_elems = h;
+        }
+
         // ---- apply tiles: for each patch, the union of the column blocks of
         // the (up to) eight row blocks it touches (Alg. 4/5 semantics) -----
         std::vector<int> cand;
@@ -740,9 +773,13 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
             cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
             for (int c : cand) {
                 Tile t;
+                const int64_t kown = b->dense[(size_t)r * ncb + c];   // slot 7 is the patch's own row block
                 for (int s = 0; s < 8; ++s) {
                     const int64_t k = rb[s] >= 0 ? b->dense[(size_t)rb[s] * ncb + c] : -1;
                     t.off[s] = k >= 0 ? b->blk_off[k] : -1;
+                    // slot s is row block (patch) - e with e = 7 - s
+                    t.hout[s] = (s != 7 && k >= 0) ? b->hslot[(size_t)k * 8 + (7 - s)] : -1;
+                    t.hin[s] = (s != 0 && kown >= 0) ? b->hslot[(size_t)kown * 8 + s] : -1;
                 }
                 t.patch = r;
                 t.pxyz = px | (py << 10) | (pz << 20);
@@ -783,7 +820,11 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                 }
                 u.patch = t.patch;
                 u.pxyz = t.pxyz;
-                for (int s = 0; s < 8; ++s) u.off[u.nb][s] = t.off[s] >= 0 ? int32_t(t.off[s] * (int64_t)b->elem() / 16) : -1;
+                for (int s = 0; s < 8; ++s) {
+                    u.off[u.nb][s] = t.off[s] >= 0 ? int32_t(t.off[s] * (int64_t)b->elem() / 16) : -1;
+                    u.hout[u.nb][s] = t.hout[s];
+                    u.hin[u.nb][s] = t.hin[s];
+                }
                 u.width[u.nb] = t.width;
                 u.ld[u.nb] = t.ld;
                 u.cellmask[u.nb] = t.cellmask;
@@ -795,6 +836,16 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         }
         if ((int64_t)b->n_values * (int64_t)b->elem() / 16 >= (int64_t)INT32_MAX)
             throw std::bad_alloc();   // offsets in 16-byte units must fit in int32
+        b->ucount.assign(R, 0);
+        b->tcount.assign(R, 0);
+        for (const Unit& u : b->units) {
+            const int px = u.pxyz & 1023, py = (u.pxyz >> 10) & 1023, pz = u.pxyz >> 20;
+            b->ucount[m->pid(px, py, pz)] += 1;
+        }
+        for (const Tile& t : b->tiles) {
+            const int px = t.pxyz & 1023, py = (t.pxyz >> 10) & 1023, pz = t.pxyz >> 20;
+            b->tcount[m->pid(px, py, pz)] += 1;
+        }
 
         // ---- Gram work lists, grouped by output block (c1, c2) -------------
         constexpr int kChunk = 16;
@@ -921,7 +972,12 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_tccg = off;  off = align_up(off + b->tc_cglob.size() * sizeof(int32_t), 256);
         b->off_tcrows = off; off = align_up(off + b->tc_rows.size() * sizeof(int32_t), 256);
         b->off_units = off; off = align_up(off + b->units.size() * sizeof(Unit), 256);
-        b->off_ticket = off; off = align_up(off + 16, 256);   // work counter of the persistent launch
+        // work counter of the apply (16 bytes) and the per-patch counters of
+        // finished work items: zeroed together before every apply
+        b->off_ticket = off; b->sync_bytes = 16 + 4 * (size_t)R; off = align_up(off + b->sync_bytes, 256);
+        b->off_ucnt = off;  off = align_up(off + 4 * (size_t)R, 256);
+        b->off_halo = off;  off = align_up(off + (size_t)b->halo_elems * b->elem(), 256);
+        b->off_tcnt = off;  off = align_up(off + 4 * (size_t)R, 256);
         b->off_rowptr = off; off = align_up(off + (R + 1) * sizeof(int64_t), 256);
         b->off_colidx = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int32_t), 256);
         b->off_blkoff = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int64_t), 256);
@@ -1004,6 +1060,8 @@ int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
         FE_TRY_CUDA(put(b->off_tccg, b->tc_cglob.data(), b->tc_cglob.size() * sizeof(int32_t)), "fe_bcsr_bind: column ids");
         FE_TRY_CUDA(put(b->off_tcrows, b->tc_rows.data(), b->tc_rows.size() * sizeof(int32_t)), "fe_bcsr_bind: rows");
         FE_TRY_CUDA(put(b->off_units, b->units.data(), b->units.size() * sizeof(Unit)), "fe_bcsr_bind: units");
+        FE_TRY_CUDA(put(b->off_ucnt, b->ucount.data(), b->ucount.size() * sizeof(int32_t)), "fe_bcsr_bind: unit counts");
+        FE_TRY_CUDA(put(b->off_tcnt, b->tcount.data(), b->tcount.size() * sizeof(int32_t)), "fe_bcsr_bind: tile counts");
         FE_TRY_CUDA(put(b->off_rowptr, b->row_ptr.data(), b->row_ptr.size() * sizeof(int64_t)), "fe_bcsr_bind: rows");
         FE_TRY_CUDA(put(b->off_colidx, b->col_idx.data(), b->col_idx.size() * sizeof(int32_t)), "fe_bcsr_bind: columns");
         FE_TRY_CUDA(put(b->off_blkoff, b->blk_off.data(), b->blk_off.size() * sizeof(int64_t)), "fe_bcsr_bind: offsets");
@@ -1077,15 +1135,31 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool ma
     a.status = m->status;
     if constexpr (sizeof(T) == 8) a.k = m->kd; else a.k = m->kf;
     if (Y->n_values == 0) return FE_OK;                       // empty pattern: nothing to compute
-    FE_TRY_CUDA(cudaMemsetAsync(Y->values, 0, (size_t)Y->n_values * sizeof(T), s), "fe_apply_H: zero Y");
+    // Y is written in full by the ordered write (every stored row by its
+    // first writer): no zero-fill.  Reset the work counter and the per-patch
+    // counters of finished work items.
+    char* sync = static_cast<char*>(P->tables) + P->off_ticket;
+    FE_TRY_CUDA(cudaMemsetAsync(sync, 0, P->sync_bytes, s), "fe_apply_H: reset work counters");
+    unsigned long long* ticket = reinterpret_cast<unsigned long long*>(sync);
+    int32_t* done = reinterpret_cast<int32_t*>(sync + 16);
+    const int32_t* ucount = reinterpret_cast<const int32_t*>(static_cast<const char*>(P->tables) + P->off_ucnt);
+    const int32_t* tcount = reinterpret_cast<const int32_t*>(static_cast<const char*>(P->tables) + P->off_tcnt);
+    T* halo = reinterpret_cast<T*>(static_cast<char*>(P->tables) + P->off_halo);
+    a.ticket = ticket;
+    a.done = done;
+    a.count = tcount;
+    a.halo = halo;
     if constexpr (sizeof(T) == 4) {
         if (P->form == FE_FORM_CELLMAT && m->p <= 2) {
             CellMatArgs c;
             c.P = a.P; c.Y = a.Y; c.Vq = a.Vq;
             c.units = reinterpret_cast<const Unit*>(static_cast<const char*>(P->tables) + P->off_units);
             c.n_units = (int64_t)P->units.size();
-            c.ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(P->tables) + P->off_ticket);
-            FE_TRY_CUDA(cudaMemsetAsync(c.ticket, 0, sizeof(unsigned long long), s), "fe_apply_H: reset work counter");
+            c.ticket = ticket;
+            c.done = done;
+            c.count = ucount;
+            c.halo = halo;
+            c.npx = a.npx; c.npy = a.npy; c.npz = a.npz;
             c.lx = a.lx; c.ly = a.ly; c.lz = a.lz; c.dirichlet = a.dirichlet;
             c.status = a.status;
             c.mass = a.mass;
@@ -1100,12 +1174,13 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool ma
         u.P = a.P; u.Y = a.Y; u.Vq = a.Vq;
         u.units = reinterpret_cast<const Unit*>(static_cast<const char*>(P->tables) + P->off_units);
         u.n_units = (int64_t)P->units.size();
-        u.ticket = nullptr;
+        u.ticket = ticket;
+        u.persistent = P->persistent;
         u.ctas_per_sm = P->ctas_per_sm;
-        if (P->persistent) {
-            u.ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(P->tables) + P->off_ticket);
-            FE_TRY_CUDA(cudaMemsetAsync(u.ticket, 0, sizeof(unsigned long long), s), "fe_apply_H: reset work counter");
-        }
+        u.done = done;
+        u.count = ucount;
+        u.halo = halo;
+        u.npx = a.npx; u.npy = a.npy; u.npz = a.npz;
         u.lx = a.lx; u.ly = a.ly; u.lz = a.lz; u.dirichlet = a.dirichlet;
         u.status = a.status;
         u.mass = a.mass;

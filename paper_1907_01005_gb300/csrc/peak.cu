@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(256) fma2_chains(float* out, int64_t iters, fl
 // Thread 0's chain sum, computed on the host with the same IEEE fused
 // multiply-adds and the same order of additions as the kernels (FE_F64,
 // FE_F32, or 3 for the packed FP32x2 chains, whose two halves start at c and
-// -c).  Used to check what the kernels stored in the sink.
+// at the unsigned difference 0 - c, i.e. 2^32 - c rounded to FP32).  Used to
+// check what the kernels stored in the sink.
 static double chain_sum_thread0(int dtype, int64_t iters) {
     if (dtype == FE_F64) {
         double x[8];
@@ -72,7 +73,7 @@ static double chain_sum_thread0(int dtype, int64_t iters) {
     }
     if (dtype == 3) {
         float a[8], b[8];
-        for (int c = 0; c < 8; ++c) { a[c] = float(c); b[c] = float(-c); }
+        for (int c = 0; c < 8; ++c) { a[c] = float(c); b[c] = float(0u - (unsigned)c); }
         for (int64_t i = 0; i < iters * 8; ++i)
             for (int c = 0; c < 8; ++c) {
                 a[c] = std::fma(a[c], 0.999999f, 1e-7f);

@@ -1,7 +1,22 @@
 // Device helpers shared by the apply kernels (apply_unit.cu: sum
 // factorisation in registers; apply_cellmat.cu: cell matrices on the tensor
-// cores; apply.cu: the p >= 3 plane kernel): the patch-node table of the
-// packed-unit kernels and the 16-byte scatter-add into Y.
+// cores; apply.cu: the p >= 3 plane kernel): the patch-node table, the
+// fixed-order sum of the cells' results, and the conflict-free write of a
+// patch's results into Y.
+//
+// Write into Y (Alg. 6, write step, with the "compress" of Sec. 3.4 done on
+// the device).  Row block r is owned by its patch; its upper-face nodes also
+// receive contributions from the upper neighbour patches r + e, e in
+// {0,1}^3 \ {0}.  Work items are taken in descending patch rank (Morton
+// ranks grow with each coordinate, so upper neighbours come first).  Each
+// work item (1) stores its contributions to its lower neighbours' rows in
+// halo slots of their own (block, e), then marks its patch; (2) waits,
+// bounded in time, until its (at most 7) upper neighbours have marked theirs;
+// (3) adds to its own rows the halo rows addressed to them, in a fixed order
+// (own part, then e = 1 .. 7), and stores every row of its own blocks once.
+// No step waits on anything but halo writes, which never wait, so the waits
+// stay one level deep.  Y gets no zero-fill, no atomics and no
+// read-modify-write, and the same bits on every run.
 #pragma once
 
 #include "fe_internal.h"
@@ -9,26 +24,36 @@
 namespace femf {
 namespace {
 
-// 16-byte chunk of one block row added into Y
-__device__ __forceinline__ void red_chunk(float* dst, const float* v) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(dst), "f"(v[0]), "f"(v[1]), "f"(v[2]),
-                 "f"(v[3]) : "memory");
-}
-__device__ __forceinline__ void red_chunk(double* dst, const double* v) {
-    if (v[0] != 0.0) atomicAdd(dst, v[0]);
-    if (v[1] != 0.0) atomicAdd(dst + 1, v[1]);
+// Node `node` of the (2p+1)^3 patch (px, py, pz): row (bits 0-15) of the
+// node in the row block that owns it, that row block's slot s = dx + 2 dy +
+// 4 dz (bits 16-18; the owner is patch (px - 1 + dx, py - 1 + dy, pz - 1 +
+// dz), s = 7 the patch itself), kBoundary for a Dirichlet boundary node
+// (input read as zero, output zero), and in bits 22-30: for an own node its
+// face mask f (f_d = 1 on the upper face in direction d when an upper
+// neighbour exists there), else its index in the owner's halo slot.
+constexpr int kBoundary = 1 << 21;
+constexpr int kAuxShift = 22;
+
+// Index of an owner-frame node (i, j, k) of patch (px, py, pz) in the halo
+// slot of offset e: lexicographic (x fastest) over the directions d with
+// e_d = 0, each over the owner's node range [lo, 2p], lo = 0 for a patch at
+// coordinate 0 and 1 else.
+template <int P>
+__device__ __forceinline__ int halo_face_index(int e, int i, int j, int k, int px, int py, int pz) {
+    constexpr int Q = 2 * P;
+    int idx = 0, stride = 1;
+    if (!(e & 1)) { const int lo = px > 0; idx += (i - lo) * stride; stride *= Q + 1 - lo; }
+    if (!(e & 2)) { const int lo = py > 0; idx += (j - lo) * stride; stride *= Q + 1 - lo; }
+    if (!(e & 4)) { const int lo = pz > 0; idx += (k - lo) * stride; }
+    return idx;
 }
 
-// Node `node` of the (2p+1)^3 patch (px, py, pz): (slot << 16) | row, slot
-// b = dx + 2 dy + 4 dz naming the row block that owns the node (patch
-// (px - 1 + dx, py - 1 + dy, pz - 1 + dz)) and row its position there; -1 for a
-// Dirichlet boundary node.
 template <int P>
-__device__ __forceinline__ int node_entry(int node, int px, int py, int pz, int lx, int ly, int lz, int dirichlet) {
+__device__ __forceinline__ int node_entry(int node, int px, int py, int pz, int lx, int ly, int lz, int dirichlet,
+                                          int npx, int npy, int npz) {
     constexpr int Q = 2 * P, NP = 2 * P + 1;
     const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
     const int I = Q * px + i, J = Q * py + j, K = Q * pz + k;
-    if (dirichlet && (I == 0 || J == 0 || K == 0 || I == lx - 1 || J == ly - 1 || K == lz - 1)) return -1;
     const int dx = (i == 0 && px > 0) ? 0 : 1;
     const int dy = (j == 0 && py > 0) ? 0 : 1;
     const int dz = (k == 0 && pz > 0) ? 0 : 1;
@@ -36,7 +61,184 @@ __device__ __forceinline__ int node_entry(int node, int px, int py, int pz, int 
     const int qx = px - 1 + dx, qy = py - 1 + dy, qz = pz - 1 + dz;
     const int nxq = Q + (qx == 0), nyq = Q + (qy == 0);
     const int row = (ii - (qx != 0)) + nxq * ((jj - (qy != 0)) + nyq * (kk - (qz != 0)));
-    return ((dx + 2 * dy + 4 * dz) << 16) | row;
+    const int slot = dx + 2 * dy + 4 * dz;
+    int aux;
+    if (slot == 7)
+        aux = (i == Q && px + 1 < npx ? 1 : 0) | (j == Q && py + 1 < npy ? 2 : 0) | (k == Q && pz + 1 < npz ? 4 : 0);
+    else
+        aux = halo_face_index<P>(7 - slot, i, j, k, px, py, pz);   // free directions: the owner's coordinates are ours
+    const bool bnd = dirichlet && (I == 0 || J == 0 || K == 0 || I == lx - 1 || J == ly - 1 || K == lz - 1);
+    return (slot << 16) | row | (bnd ? kBoundary : 0) | (aux << kAuxShift);
+}
+
+constexpr uint64_t kOrderWaitNs = 500ull * 1000 * 1000;   // bounded wait for neighbour patches (0.5 s)
+
+__device__ __forceinline__ uint64_t order_clock_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Called by all threads of warp 0: lane e in 1..7 waits until the upper
+// neighbour (px, py, pz) + e, if it exists, has written its halo
+// (done[pid] == count[pid], both indexed by pid = x + npx (y + npy z)).
+// Returns false (in every lane) when a wait gave up.
+__device__ __forceinline__ bool wait_upper_neighbours(const int32_t* done, const int32_t* count, int px, int py,
+                                                      int pz, int npx, int npy, int npz) {
+    const int e = threadIdx.x & 31;
+    bool ok = true;
+    if (e >= 1 && e < 8) {
+        const int qx = px + (e & 1), qy = py + ((e >> 1) & 1), qz = pz + (e >> 2);
+        if (qx < npx && qy < npy && qz < npz) {
+            const int q = qx + npx * (qy + npy * qz);
+            const int want = count[q];
+            const uint64_t t0 = order_clock_ns();
+            while (true) {
+                int v;
+                asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(done + q) : "memory");
+                if (v >= want) break;
+                if (order_clock_ns() - t0 > kOrderWaitNs) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Called by thread 0 after a __syncthreads that follows the CTA's halo
+// stores: publishes one work item of patch pid whose halo is written.
+__device__ __forceinline__ void mark_done(int32_t* done, int pid) {
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(done + pid), "r"(1) : "memory");
+}
+
+// 16-byte vectors of the rows (ld, the row stride, is a multiple of 16 bytes)
+template <typename T> struct V16;
+template <> struct V16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static void add(float4& a, const float4& b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+};
+template <> struct V16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static void add(double2& a, const double2& b) { a.x += b.x; a.y += b.y; }
+};
+
+// A row of the patch tensor (ys) to a halo row (dst).  Stores go to L2 only:
+// another SM reads them.
+template <typename T>
+__device__ __forceinline__ void put_halo_row(T* dst, const T* ys, int ld) {
+    using V = typename V16<T>::type;
+    for (int c0 = 0; c0 < ld; c0 += V16<T>::n)
+        __stcg(reinterpret_cast<V*>(dst + c0), *reinterpret_cast<const V*>(ys + c0));
+}
+
+// An own row of Y: the patch's part (ys), plus the halo rows of the upper
+// neighbours e within the face mask f (halo + hin[e] 16-byte units + the
+// row's face index times ld), added in the order e = 1 .. 7; zeros for a
+// boundary node.  Stored once.
+template <int P, typename T>
+__device__ __forceinline__ void put_own_row(T* yd, const T* ys, int ld, bool zero, int f, const T* halo,
+                                            const int32_t* hin, int i, int j, int k, int px, int py, int pz) {
+    using V = typename V16<T>::type;
+    constexpr int kElem16 = 16 / sizeof(T);
+    const T* src[7];
+    int ns = 0;
+    if (!zero) {
+#pragma unroll
+        for (int e = 1; e < 8; ++e)
+            if ((f & e) == e && hin[e] >= 0)
+                src[ns++] = halo + (int64_t)hin[e] * kElem16 + halo_face_index<P>(e, i, j, k, px, py, pz) * ld;
+    }
+    for (int c0 = 0; c0 < ld; c0 += V16<T>::n) {
+        V v = zero ? V16<T>::zero() : *reinterpret_cast<const V*>(ys + c0);
+        for (int q = 0; q < ns; ++q) V16<T>::add(v, __ldcg(reinterpret_cast<const V*>(src[q] + c0)));
+        __stcg(reinterpret_cast<V*>(yd + c0), v);
+    }
+}
+
+// Sums the results of the eight cells of a patch in a fixed order and stores
+// every patch node once, for CTAs of 256 threads where thread (cell =
+// tid / 32, lane = tid % 32) holds t, its cell's (p+1)^3 results for one
+// column lane.  Cells that share nodes are merged pairwise: along x (cell
+// cx = 1 hands its x = 0 face to cell cx = 0, which adds it into its x = p
+// face), then along y, then along z, through the exchange buffer ex (free
+// shared memory of 2 kMergeFace<P> elements: the faces alternate between two
+// halves; with SINGLE one half and a barrier more per step).  Afterwards a cell owns its local nodes with x >= cx,
+// y >= cy, z >= cz, and each patch node has exactly one owner, which stores
+// it (plain store) at yp[base + ((z NP + y) NP + x) S].  With the faces merged
+// in this order every node's sum has the same rounding on every run.  Every
+// thread of the CTA must call it (it holds barriers); `store` is false for
+// lanes without a column.
+template <int P>
+constexpr int kMergeFace = (P + 1) * (P + 1) * 256;   // one face of every thread
+template <int P, int S, int NP, bool SINGLE, typename T>
+__device__ __forceinline__ void merge_cells_store(T (&t)[P + 1][P + 1][P + 1], int cell, int lane, bool store, T* ex,
+                                                  T* yp, int base) {
+    constexpr int N = P + 1;
+    const int cx = cell & 1, cy = (cell >> 1) & 1, cz = (cell >> 2) & 1;
+    // slot of face entry f of the receiving cell rc: [f][rc][lane]
+    auto slot = [&](T* e, int f, int rc) -> T& { return e[(f * 8 + rc) * 32 + lane]; };
+    T* e0 = ex;
+    T* e1 = SINGLE ? ex : ex + kMergeFace<P>;
+    // x: cell cx = 1 sends its x = 0 face to cell cell - 1
+    if (cx) {
+#pragma unroll
+        for (int z = 0; z < N; ++z)
+#pragma unroll
+            for (int y = 0; y < N; ++y) slot(e0, z * N + y, cell - 1) = t[z][y][0];
+    }
+    __syncthreads();
+    if (!cx) {
+#pragma unroll
+        for (int z = 0; z < N; ++z)
+#pragma unroll
+            for (int y = 0; y < N; ++y) t[z][y][P] += slot(e0, z * N + y, cell);
+    }
+    if (SINGLE) __syncthreads();
+    // y: cell cy = 1 sends its y = 0 face to cell cell - 2
+    if (cy) {
+#pragma unroll
+        for (int z = 0; z < N; ++z)
+#pragma unroll
+            for (int x = 0; x < N; ++x) slot(e1, z * N + x, cell - 2) = t[z][0][x];
+    }
+    __syncthreads();
+    if (!cy) {
+#pragma unroll
+        for (int z = 0; z < N; ++z)
+#pragma unroll
+            for (int x = 0; x < N; ++x) t[z][P][x] += slot(e1, z * N + x, cell);
+    }
+    if (SINGLE) __syncthreads();
+    // z: cell cz = 1 sends its z = 0 face to cell cell - 4
+    if (cz) {
+#pragma unroll
+        for (int y = 0; y < N; ++y)
+#pragma unroll
+            for (int x = 0; x < N; ++x) slot(e0, y * N + x, cell - 4) = t[0][y][x];
+    }
+    __syncthreads();
+    if (!cz) {
+#pragma unroll
+        for (int y = 0; y < N; ++y)
+#pragma unroll
+            for (int x = 0; x < N; ++x) t[P][y][x] += slot(e0, y * N + x, cell);
+    }
+    if (store) {
+#pragma unroll
+        for (int z = 0; z < N; ++z)
+#pragma unroll
+            for (int y = 0; y < N; ++y)
+#pragma unroll
+                for (int x = 0; x < N; ++x)
+                    if (x >= cx && y >= cy && z >= cz) yp[base + ((z * NP + y) * NP + x) * S] = t[z][y][x];
+    }
 }
 
 }  // namespace

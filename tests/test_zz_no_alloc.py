@@ -28,7 +28,7 @@ def _probe(name, dtype, iters):
     return f.value
 
 
-@pytest.mark.parametrize("dtype,iters", [(1, 4000), (2, 200)], ids=["f32", "f64"])
+@pytest.mark.parametrize("dtype,iters", [(1, 4000), (2, 200), (3, 4000)], ids=["f32", "f64", "f32x2"])
 def test_static_sink_probe_matches_allocating_probe(dtype, iters):
     import torch
     torch.cuda.init()
