@@ -305,6 +305,8 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
             put_own_row<P>(a.Y + oown + (int64_t)(ne & 0xffff) * ld, Yp + node * ld, ld, (ne & kBoundary) != 0,
                            (ne >> kAuxShift) & 7, a.halo, sHin, i, j, k, px, py, pz);
         }
+        __syncthreads();                               // the halo rows addressed to this tile are read
+        if (threadIdx.x < 32) discard_halo<P>(a.halo, sHin, ld, px, py, pz, threadIdx.x, 32);   // one warp
     }
 }
 

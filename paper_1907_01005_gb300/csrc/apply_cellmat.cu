@@ -467,6 +467,10 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                 put_own_row<P>(a.Y + (int64_t)o * 4 + (ne & 0xffff) * ldb, U + node * S + sBase[bb], ldb,
                                (ne & kBoundary) != 0, (ne >> kAuxShift) & 7, a.halo, sHin[bb], i, j, k, px, py, pz);
             }
+            __syncthreads();                               // the halo rows addressed to this unit are read
+            if (warp == 7)                                 // one warp drops them from L2
+                for (int bb = 0; bb < nb; ++bb)
+                    if (sOff[bb][7] >= 0) discard_halo<P>(a.halo, sHin[bb], sLd[bb], px, py, pz, tid & 31, 32);
         }  // unit_ok
         else if (tid == 0 && in_mesh) {
             mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it

@@ -270,6 +270,10 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         put_own_row<P>(a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld, Yp + node * S + sBase[b], ld,
                        (ne & kBoundary) != 0, (ne >> kAuxShift) & 7, a.halo, sHin[b], i, j, k, px, py, pz);
     }
+    __syncthreads();                                   // the halo rows addressed to this unit are read
+    if (tid >= (int)blockDim.x - 32)                   // one warp drops them from L2
+        for (int b = 0; b < nb; ++b)
+            if (sOff[b][7] >= 0) discard_halo<P>(a.halo, sHin[b], sLd[b], px, py, pz, tid & 31, 32);
     }  // unit_ok
     else if (tid == 0 && in_mesh) {
         mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it

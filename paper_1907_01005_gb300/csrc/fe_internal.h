@@ -96,7 +96,8 @@ struct GramItem {
 
 // Tensor-core Gram of FP32 multivectors (gram_tc.cu): work is grouped by
 // runs of consecutive row blocks; a group's union of column blocks is laid
-// out as `width` dense columns, and its output is tiled 32 x 32.
+// out as `width` dense columns, its output tiled gram_tc_tile() square and
+// its rows split into items of at most gram_tc_item_rows().
 constexpr int kMaxGroup = 8;     // row blocks per group
 constexpr int kMaxUnion = 64;    // column blocks in a group's union
 struct GramTcGroup {
@@ -111,7 +112,7 @@ struct GramTcGroup {
 struct GramTcItem {
     int32_t group;
     int32_t tile;       // mi | ni << 16 (square tiles of gram_tc_tile() union columns)
-    int32_t k0, k1;     // rows [k0, k1) of the group (split at gram_tc_split_rows())
+    int32_t k0, k1;     // rows [k0, k1) of the group (at most gram_tc_item_rows())
 };
 struct GramTcArgs {
     const float* A;
@@ -119,6 +120,7 @@ struct GramTcArgs {
     const GramTcGroup* groups;
     const GramTcItem* items;
     int64_t n_items;
+    int64_t n_items_diag;       // P^T P: the first n_items_diag items are diagonal tiles (mi == ni)
     const int64_t* union_off;   // element offset of block (row block, union slot) or -1
     const int32_t* col_info;    // (slot << 16) | (column in block << 8) | row stride of the block
     const int32_t* col_glob;    // global column id
@@ -131,8 +133,8 @@ struct GramTcArgs {
 // known to be symmetric (closed pattern), upper super-tiles, mirrored
 enum class GramMode { PtY = 0, PtP = 1, PtYSym = 2 };
 cudaError_t launch_gram_tc(const GramTcArgs& a, GramMode mode, cudaStream_t s);
-int gram_tc_tile();         // output super-tile edge of the tensor-core Gram
-int gram_tc_split_rows();   // rows per work item (multiple of every window height)
+int gram_tc_tile();         // output tile edge of the tensor-core Gram (union columns)
+int gram_tc_item_rows(bool pp);   // most rows of a work item of P^T P (pp) or P^T Y
 
 template <typename T>
 struct ApplyArgs {

@@ -2,46 +2,58 @@
 // error-free split (C = A^T B over stored blocks, Alg. 8; FP64-accurate
 // result).
 //
-// Numerics.  Rows are taken in windows of at most KX rows.  In a window every
-// FP32 value x of union column m is normalised by the window's power-of-two
-// bound 2^E (|x| < 2^E, E per column and window) and written as a sum of
-// bf16 slices y_s (every slice exact in bf16, every slice product exact in
-// FP32):
+// Numerics.  Work items are runs of at most 192 (P^T P) or 256 (P^T Y) rows
+// of a group of consecutive row blocks.  In an item every FP32 value x of union column m
+// is normalised by the item's power-of-two bound 2^E_m (|x| < 2^E_m) and
+// written as a sum of bf16 slices y_s (every slice exact in bf16, every slice
+// product exact in FP32):
 //   P^T P  five slices on fixed grids, y_s = q_s 2^(-8 s), |q_1| <= 256,
-//          |q_s| <= 128 for s >= 2; products with s + t <= 6 are kept;
+//          |q_s| <= 128 for s >= 2; products with s + t <= 6 are kept (four
+//          slices, s + t <= 5, were measured at 2e-9, above the tolerance);
 //   P^T Y  y_1 = q_1 2^-8 on the fixed grid, y_2, y_3 the bf16 roundings of
 //          the remainders ("natural" slices); products with s + t <= 4.
 // The product of slices s and t has level L = s + t.  The tensor cores sum
-// each level class of a window in an FP32 accumulator in tensor memory:
-//   P^T P  levels 2, 3 and 4 each on its own: their window sums are integers
-//          (units 2^-16, 2^-24, 2^-32) below 2^24 for KX = 192 rows, hence
-//          exact whatever the rounding of the tensor-core adder; levels 5 and
-//          6 together, below 2^-24 of the result per row, so their FP32
-//          rounding is immaterial;
-//   P^T Y  level 2 exact (KX = 256 rows), levels 3 and 4 together.
-// After each window the class sums are converted to integers in units of
-// 2^-(8 LMAX) and added into an int64 per output element, scaled by
-// 2^(E_m(w) + E_n(w)) relative to a running per-column reference exponent R
-// (the largest window exponent so far): the accumulator is shifted right when
-// R grows, the window value when its exponents are below R.  The int64 is
-// converted to FP64 with integer operations only (the FP64 pipe of this GPU
-// is slow) and added into the dense FP64 result with one atomic per element.
+// each level class of an item in an FP32 accumulator in tensor memory:
+//   P^T P  levels 2, 3 and 4 each on its own: their sums are integers (units
+//          2^-16, 2^-24, 2^-32) below 2^24 over 192 rows (level 4: at most
+//          (2^15 + 2^14 + 2^15) 192 < 2^24), hence exact whatever the rounding
+//          of the tensor-core adder; levels 5 and 6, below 2^-23 of the
+//          bound products per row, in a fourth class whose FP32 rounding is
+//          immaterial;
+//   P^T Y  level 2 exact (its sum is at most 2^16 256 = 2^24 units of 2^-16
+//          over 256 rows), levels 3 and 4 together.
+// The epilogue turns the class sums of an output element into one integer in
+// units of 2^-(8 LMAX) of 2^(E_m + E_n), converts it to FP64 with integer
+// operations only (the FP64 pipe of this GPU is slow) and adds it into the
+// dense FP64 result with one atomic (and its mirror for symmetric products).
 //
-// Work item: (group of consecutive row blocks, 128 x 128 tile (mi, ni) of the
-// group's union columns, range of the group's rows).  Operand A of the MMA is
-// the panel of the tile's 128 A columns (M = 128 rows of the MMA, one per
-// union column, K = rows of the multivector), operand B the panel of its
-// N <= 128 B columns; D[m][n] = sum_k A[m][k] B[n][k] lands in tensor-memory
-// lane m, column n (+ 128 per level class).  Panels are staged 64 rows at a
-// time as bf16 slices in the K-major layout with the 128-byte swizzle (an
-// operand row is 64 bf16 = 128 bytes), into one of two buffers, so that the
-// slicing of chunk c+1 overlaps the MMAs of chunk c.  One thread issues the
-// tcgen05.mma instructions and commits them to the buffer's mbarrier; all
-// sixteen warps stage, and all sixteen read the accumulators back
-// (tcgen05.ld: warp w reaches lanes 32 (w % 4) .. + 31 and takes 32 of the
-// tile's columns).  Every wait on an mbarrier is bounded in time; on a
-// time-out the kernel sets the status word, waits (bounded) for the MMAs in
-// flight, frees its tensor memory and returns.
+// Tiles.  An item computes a 128 x N tile (mi, ni) of its group's union
+// columns: operand A of the MMA is the panel of the tile's 128 A columns
+// (M = 128 rows of the MMA, one per union column; K = rows of the
+// multivector), operand B the panel of its N <= 128 B columns, and
+// D[m][n] = sum_k A[m][k] B[n][k] lands in tensor-memory lane m, column n
+// (+ 128 per level class).  Panels are staged 64 rows at a time as bf16
+// slices in the K-major layout with the 128-byte swizzle (an operand row is
+// 64 bf16 = 128 bytes).
+//
+// Pipeline.  A persistent CTA per SM takes items in a fixed stride and runs
+// three roles at once, handing over through mbarriers:
+//   producers (16 warps) per item: the group's tables, the column bounds and
+//                        exponents; then per 64-row chunk: load, normalise,
+//                        slice into a free stage of a two-stage ring;
+//   MMA issuer (1 lane)  per chunk: waits for the stage, issues the slice
+//                        products (tcgen05.mma kind::f16, bf16 -> FP32),
+//                        commits them to free the stage; per item: commits
+//                        the accumulators to the epilogue;
+//   epilogue (8 warps)   per item: reads the accumulators back (tcgen05.ld;
+//                        warp w reaches lanes 32 (w % 4) .. + 31 and takes
+//                        half of the tile's columns), releases them, and
+//                        adds the results into G.
+// P^T Y keeps two accumulator sets in tensor memory, so the epilogue of an
+// item overlaps the MMAs of the next; P^T P (four classes) has one.  Every
+// mbarrier wait is bounded in time: on a time-out the kernel sets the status
+// word, and every role leaves its loop; the MMA issuer waits (bounded) for its
+// MMAs in flight before the tensor memory is freed.
 #include <cuda_bf16.h>
 
 #include "fe_internal.h"
@@ -50,11 +62,18 @@ namespace femf {
 namespace {
 
 constexpr int kST = 128;                  // output tile edge in union columns (M of the MMA, N <= kST)
-constexpr int kThreads = 512;             // 16 warps
 constexpr int kKC = 64;                   // rows of a staged chunk: 64 bf16 = one 128-byte swizzle row
+// rows of a work item: the level classes summed exactly stay below 2^24
+constexpr int kItemRowsPP = 192;          // P^T P (level 4: (2^15 + 2^14 + 2^15) 192 < 2^24)
+constexpr int kItemRowsPY = 256;          // P^T Y (level 2: 2^16 256 = 2^24)
 constexpr int kPanel = kST * 128;         // bytes of one slice panel (128 operand rows of 128 bytes)
-constexpr int kBuf = 96 * 1024;           // bytes of one staging buffer (both operands of a chunk)
-constexpr int kSmemDyn = 2 * kBuf + 1024; // two buffers + slack for the 1024-byte alignment
+constexpr int kStage = 96 * 1024;         // bytes of one ring stage (both operands of a chunk)
+constexpr int kProdWarps = 16, kEpiWarps = 8;
+constexpr int kMmaWarp = kProdWarps + kEpiWarps;          // warp 24
+constexpr int kThreads = 32 * (kMmaWarp + 1);            // 800
+static_assert(kProdWarps % 4 == 0, "the epilogue warps must cover the four tensor-memory lane quadrants in order");
+constexpr int kProdThreads = 32 * kProdWarps, kEpiThreads = 32 * kEpiWarps;
+constexpr int kBarProd = 1, kBarEpi = 2, kBarQuad = 3;   // named barriers: warp groups, quad numbering
 constexpr int kNone = -30000;             // exponent of an all-zero column
 constexpr int kMaxRows = (2 * kMaxP + 1) * (2 * kMaxP + 1) * (2 * kMaxP + 1);   // rows of a row block
 constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;   // bounded mbarrier waits (0.2 s)
@@ -220,6 +239,52 @@ __device__ __forceinline__ float load8(const float* __restrict__ X, int ci, cons
     return mx;
 }
 
+// Loads rows kstart .. kstart+7 of the group (those at or past kend read as
+// zero) of one 16-byte quad of a union block (slot u, block columns a0 ..
+// a0 + 3; consecutive rows of a row block are ld elements apart) as float4.
+__device__ __forceinline__ void load8q(const float* __restrict__ X, int u, int a0, int ld, const int64_t* sOff,
+                                       int n_u, const int* sPref, int nrb, int kstart, int kend, float4 (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (kstart >= kend) return;
+    int r = 0;
+    while (r < nrb - 1 && kstart >= sPref[r + 1]) ++r;
+    int e = sPref[r + 1];
+    int64_t o = sOff[r * n_u + u];
+    int64_t idx = o + (int64_t)(kstart - sPref[r]) * ld + a0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k = kstart + i;
+        if (k < kend) {
+            if (k == e) {                     // first row of the next row block (k < kend <= sPref[nrb])
+                ++r;
+                e = sPref[r + 1];
+                o = sOff[r * n_u + u];
+                idx = o + a0;
+            }
+            if (o >= 0) v[i] = __ldg(reinterpret_cast<const float4*>(X + idx));
+            idx += ld;
+        }
+    }
+}
+
+// Component i of a float4
+__device__ __forceinline__ float f4c(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
+// A quad of the tile: the 16-byte chunk (block columns a0 .. a0 + 3) of union
+// block u's rows that holds tile columns tc0 .. tc0 + 3; bit i of mask is set
+// when block column a0 + i is tile column tc0 + i (not row padding, not
+// outside the tile)
+struct Quad {
+    int u, a0, ld, mask, tc0;
+};
+__device__ __forceinline__ int quad_pack(int u, int a0, int ld, int mask, int tc0) {
+    return u | (a0 << 6) | (ld << 11) | (mask << 19) | ((tc0 + 4) << 23);
+}
+__device__ __forceinline__ Quad quad_unpack(int q) {
+    return Quad{q & 63, (q >> 6) & 31, (q >> 11) & 255, (q >> 19) & 15, ((q >> 23) & 255) - 4};
+}
+
 // Byte offset of 16-byte chunk j (rows 8j .. 8j+7 of the chunk) of operand
 // row c in a slice panel: the 128-byte swizzle (chunk index XOR row mod 8)
 __device__ __forceinline__ uint32_t sw_off(int c, int j) { return (uint32_t)(c * 128 + ((j ^ (c & 7)) << 4)); }
@@ -279,86 +344,110 @@ __host__ __device__ constexpr int level_class(int L) {
     return NCLS == 4 ? (L <= 4 ? L - 2 : 3) : (L == 2 ? 0 : 1);
 }
 
-// The window value of one output element from its class sums, as an integer
-// in units of 2^-(8 LMAX) of 2^(E_m + E_n)
-template <int NCLS>
+// The item value of one output element from its class sums, as an integer
+// in units of 2^-U (U = 8 LMAX) of 2^(E_m + E_n)
+template <int NCLS, int U>
 __device__ __forceinline__ long long window_value(const float (&c)[NCLS]) {
-    if constexpr (NCLS == 4) {   // P^T P, units 2^-48
+    if constexpr (NCLS == 4) {   // P^T P: levels 2, 3, 4 exact integers, the rest small
         const int i2 = __float2int_rn(c[0] * pow2f(16));
         const int i3 = __float2int_rn(c[1] * pow2f(24));
         const int i4 = __float2int_rn(c[2] * pow2f(32));
-        return ((long long)i2 << 32) + ((long long)i3 << 24) + ((long long)i4 << 16) + round_scaled_i64<48, 32>(c[3]);
-    } else {                     // P^T Y, units 2^-32
+        return ((long long)i2 << (U - 16)) + ((long long)i3 << (U - 24)) + ((long long)i4 << (U - 32)) +
+               round_scaled_i64<U, U - 16>(c[3]);
+    } else {                     // P^T Y: level 2 exact, the rest
         const int i2 = __float2int_rn(c[0] * pow2f(16));
-        return ((long long)i2 << 16) + round_scaled_i64<32, 16>(c[1]);
+        return ((long long)i2 << (U - 16)) + round_scaled_i64<U, U - 16>(c[1]);
     }
 }
 
-template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, int KX, bool NAT>
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// named barrier of one warp group (all of its warps converged)
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+    __syncwarp();
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Item geometry shared by the three roles
+struct ItemGeo {
+    bool ok;          // the work-list check passed
+    int mi, ni, nrb;
+    int wa, wb, N;    // A columns, B columns, MMA N
+    bool diag, share;
+    int nchunks;
+};
+template <bool SYM, bool SAME, int ROWS>
+__device__ __forceinline__ ItemGeo item_geo(const GramTcItem& it, const GramTcGroup& gr) {
+    ItemGeo g;
+    g.mi = it.tile & 0xffff;
+    g.ni = it.tile >> 16;
+    g.nrb = gr.r1 - gr.r0;
+    // work-list check: a group has 1..kMaxGroup row blocks of at most kMaxRows
+    // rows and 1..kMaxUnion union column blocks (the shared tables depend on
+    // it), an item at most ROWS rows
+    g.ok = g.nrb >= 1 && g.nrb <= kMaxGroup && gr.n_u >= 1 && gr.n_u <= kMaxUnion && gr.width >= 1 &&
+           gr.width <= kMaxUnion * kMaxW && gr.k_rows <= kMaxGroup * kMaxRows && g.mi * kST < gr.width &&
+           g.ni * kST < gr.width && !(SYM && g.mi > g.ni) && it.k0 >= 0 && it.k1 <= gr.k_rows && it.k0 < it.k1 &&
+           it.k1 - it.k0 <= ROWS && (!SAME || g.mi == g.ni);
+    g.wa = min(kST, gr.width - g.mi * kST);
+    g.wb = min(kST, gr.width - g.ni * kST);
+    g.N = (g.wb + 15) & ~15;
+    g.diag = SYM && g.mi == g.ni;
+    g.share = SAME;
+    g.nchunks = (it.k1 - it.k0 + kKC - 1) / kKC;
+    return g;
+}
+
+// Metadata of an item that the epilogue needs: global column ids and the
+// item exponents of the tile's A and B columns
+struct ItemMeta {
+    int gcol[2][kST];
+    int E[2][kST];
+};
+
+// SAME: P^T P on diagonal tiles, A = B (one panel); SA, SB slices; LMAX the
+// highest level kept; NCLS level classes; SYM upper tiles mirrored; NAT the
+// natural three-slice split; NST ring stages (2: a chunk in one 96 KB stage;
+// 1: the two operands of a P^T P off-diagonal chunk across the whole 192 KB)
+template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS>
 __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g) {
-    static_assert(KX % kKC == 0, "windows are whole chunks");
     static_assert(!NAT || (SA == 3 && SB == 3), "natural slices: three per operand");
     static_assert(NCLS * kST <= 512, "tensor memory: 128 columns per level class");
-    constexpr int TMEM_COLS = NCLS * kST;       // 256 or 512 (a power of two)
-    constexpr int U = 8 * LMAX;                 // the flush works in units of 2^-U
+    constexpr int NSETS = 512 / (NCLS * kST);   // accumulator sets in tensor memory
+    constexpr int U = 8 * LMAX;                 // the epilogue works in units of 2^-U
+    constexpr int bytesA = SA * kPanel, bytesB = SB * kPanel;
+    static_assert(NST == 2 ? (SAME ? bytesA : bytesA + bytesB) <= kStage : bytesA + bytesB <= 2 * kStage,
+                  "a chunk fits its stage");
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    unsigned char* sm = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
+    unsigned char* ring = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
     __shared__ int64_t sOff[kMaxGroup * kMaxUnion];
-    __shared__ int sCol[2][kST], sGcol[2][kST];
+    __shared__ int sCol[2][kST];
+    __shared__ int sQuad[2][kST], sNq[2], sWcnt[8];
     __shared__ int sPref[kMaxGroup + 1];
     __shared__ unsigned sMax[2][kST];
-    __shared__ int sR[2][kST], sDR[2][kST], sDW[2][kST];
     __shared__ float sF1[2][kST], sF2[2][kST];
-    __shared__ __align__(8) uint64_t sBar[2];
+    __shared__ ItemMeta sMeta[2];
+    __shared__ __align__(8) uint64_t bFull[2], bEmpty[2], bTFull[2], bTEmpty[2], bMFull[2], bMEmpty[2];
     __shared__ uint32_t sTmem;
-    __shared__ int sFail;
+    __shared__ volatile int sFail;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const GramTcItem it = g.items[blockIdx.x];
-    const GramTcGroup gr = g.groups[it.group];
-    const int mi = it.tile & 0xffff, ni = it.tile >> 16;
-    const int nrb = gr.r1 - gr.r0;
-    // Work-list check: a group has 1..kMaxGroup row blocks of at most kMaxRows
-    // rows and 1..kMaxUnion union column blocks (the shared tables depend on
-    // it); a malformed item sets the status word and leaves G untouched.
-    if (nrb < 1 || nrb > kMaxGroup || gr.n_u < 1 || gr.n_u > kMaxUnion || gr.width < 1 ||
-        gr.width > kMaxUnion * kMaxW || gr.k_rows > kMaxGroup * kMaxRows || mi * kST >= gr.width ||
-        ni * kST >= gr.width || (SYM && mi > ni) || it.k0 < 0 || it.k1 > gr.k_rows || it.k0 >= it.k1) {
-        if (tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
-        return;
-    }
-    const bool diag = SYM && mi == ni;          // diagonal tile of a symmetric product
-    const bool share = SAME && mi == ni;        // ... whose B columns are A's own (B = A)
-    const int wa = min(kST, gr.width - mi * kST);          // A columns of the tile
-    const int wb = min(kST, gr.width - ni * kST);          // B columns of the tile
-    const int N = (wb + 15) & ~15;                         // MMA N (multiple of 16, <= 128)
-    // staging buffers: both operands of a chunk in one 96 KB buffer (two
-    // buffers, chunks alternate), or for P^T P off-diagonal tiles (160 KB)
-    // one buffer spanning both
-    constexpr int bytesA = SA * kPanel, bytesB = SB * kPanel;
-    const int nbuf = (share ? bytesA : bytesA + bytesB) <= kBuf ? 2 : 1;
-
-    // ---- group tables, tensor memory, barriers ------------------------------------
-    for (int e = tid; e < nrb * gr.n_u; e += kThreads) sOff[e] = g.union_off[gr.u_base + e];
-    if (tid < kST) {
-        const int ma = mi * kST + tid, nb = ni * kST + tid;
-        sCol[0][tid] = tid < wa ? g.col_info[gr.c_base + ma] : -1;
-        sGcol[0][tid] = tid < wa ? g.col_glob[gr.c_base + ma] : -1;
-        sCol[1][tid] = tid < wb ? g.col_info[gr.c_base + nb] : -1;
-        sGcol[1][tid] = tid < wb ? g.col_glob[gr.c_base + nb] : -1;
-        sR[0][tid] = sR[1][tid] = kNone;
-    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        sPref[0] = 0;
-        for (int r = 0; r < nrb; ++r) sPref[r + 1] = sPref[r] + g.rows[gr.r0 + r];
-        sFail = 0;
-        for (int b = 0; b < 2; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sBar[b])) : "memory");
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bFull[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bEmpty[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bTFull[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bTEmpty[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bMFull[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bMEmpty[b])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sFail = 0;
     }
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sTmem)),
-                     "r"(TMEM_COLS)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -366,222 +455,323 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sTmem;
-    const bool tables_ok = sPref[nrb] == gr.k_rows;   // the row walk relies on it
-    if (!tables_ok && tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
 
-    // this thread's share of the read-back: tensor-memory lane m (operand-A
-    // column), columns [32 q, 32 q + 32) of the tile
-    const int m = 32 * (warp & 3) + (tid & 31);
-    const int q = warp >> 2;
-    // warps whose columns lie wholly below the diagonal of a diagonal tile,
-    // or beyond the tile's B columns, have nothing to read back
-    const bool flush_act = 32 * q < N && !(diag && 32 * q + 31 < 32 * (warp & 3));
-    long long acc[32];
+    if (warp < kProdWarps) {
+        // ======================= producers =======================================
+        int chunk_no = 0;
+        const int side_t = tid >> 7, c_t = tid & (kST - 1);    // this thread's tile column at table set-up
+        for (int64_t item = blockIdx.x, il = 0; item < g.n_items; item += gridDim.x, ++il) {
+            const GramTcItem it = g.items[item];
+            const GramTcGroup gr = g.groups[it.group];
+            const ItemGeo ig = item_geo<SYM, SAME, ROWS>(it, gr);
+            if (!ig.ok) {
+                if (tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
+                continue;
+            }
+            const int slot = (int)(il & 1);
+            const int nsides = SAME ? 1 : 2;
+            group_sync(kBarProd, kProdThreads);              // the previous item's tables are done with
+            for (int e = tid; e < ig.nrb * gr.n_u; e += kProdThreads) sOff[e] = g.union_off[gr.u_base + e];
+            if (warp == 0) {                                  // row prefix of the group: a warp scan
+                int v = lane < ig.nrb ? g.rows[gr.r0 + lane] : 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0;
-
-    uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {false, false};
-    int chunk_no = 0;
-    const uint32_t idesc = bf16_idesc(128, N);
-
-    for (int w0 = it.k0; tables_ok && w0 < it.k1; w0 += KX) {
-        const int w1 = min(it.k1, w0 + KX);
-        // ---- pass 1: column bounds of the window ----------------------------------
-        if (tid < kST) sMax[0][tid] = sMax[1][tid] = 0u;
-        __syncthreads();
-        {
-            const int nchunks8 = (w1 - w0 + 7) >> 3;
-            for (int side = 0; side < (share ? 1 : 2); ++side) {
-                const int wc = side ? wb : wa;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += y;
+                }
+                if (lane == 0) sPref[0] = 0;
+                if (lane < ig.nrb) sPref[lane + 1] = v;
+            }
+            // tile columns: A columns on threads 0..127, B columns on 128..255
+            const bool tab = tid < 2 * kST;
+            const int wc_t = side_t ? ig.wb : ig.wa;
+            const int ci_t = tab && c_t < wc_t ? g.col_info[gr.c_base + (side_t ? ig.ni : ig.mi) * kST + c_t] : -1;
+            if (tab) {
+                sCol[side_t][c_t] = ci_t;
+                sMax[side_t][c_t] = 0u;
+            }
+            group_sync(kBarProd, kProdThreads);
+            // quads: one per tile column that starts a 16-byte chunk of its
+            // block row (or starts the tile), numbered with warp ballots; the
+            // mask marks the chunk's columns that are tile columns of that block
+            if (warp < 8) {                                   // warps 0-3: A side, 4-7: B side
+                const int a = (ci_t >> 8) & 0xff;
+                const bool head = ci_t >= 0 && ((a & 3) == 0 || c_t == 0);
+                const unsigned bal = __ballot_sync(0xffffffffu, head);
+                if (lane == 0) sWcnt[warp] = __popc(bal);
+                asm volatile("bar.sync %0, %1;" ::"r"(kBarQuad), "r"(256) : "memory");
+                if (head) {
+                    int pos = __popc(bal & ((1u << lane) - 1));
+                    for (int w = 4 * side_t; w < warp; ++w) pos += sWcnt[w];
+                    const int u = ci_t >> 16, a0 = a & ~3, tc0 = c_t - (a & 3);
+                    int mask = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int tc = tc0 + i;
+                        if (tc >= 0 && tc < wc_t && (sCol[side_t][tc] >> 16) == u) mask |= 1 << i;
+                    }
+                    sQuad[side_t][pos] = quad_pack(u, a0, ci_t & 0xff, mask, tc0);
+                }
+                if (c_t == 0)
+                    sNq[side_t] = sWcnt[4 * side_t] + sWcnt[4 * side_t + 1] + sWcnt[4 * side_t + 2] + sWcnt[4 * side_t + 3];
+            }
+            group_sync(kBarProd, kProdThreads);
+            // ---- column bounds of the item's rows: tasks (quad, 8-row group) ------
+            const int ngr = (it.k1 - it.k0 + 7) >> 3;
+            for (int side = 0; side < nsides; ++side) {
                 const float* X = side ? g.B : g.A;
-                for (int t = tid; t < wc * nchunks8; t += kThreads) {
-                    const int c = t % wc, j = t / wc;
-                    float v[8];
-                    const float mx = load8(X, sCol[side][c], sOff, gr.n_u, sPref, nrb, w0 + 8 * j, w1, v);
-                    if (mx > 0.f) atomicMax(&sMax[side][c], __float_as_uint(mx));
+                const int nq = sNq[side];
+                for (int t = tid; t < nq * ngr; t += kProdThreads) {
+                    const Quad qd = quad_unpack(sQuad[side][t % nq]);
+                    float4 v[8];
+                    load8q(X, qd.u, qd.a0, qd.ld, sOff, gr.n_u, sPref, ig.nrb, it.k0 + 8 * (t / nq), it.k1, v);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (!((qd.mask >> i) & 1)) continue;
+                        float mx = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) mx = fmaxf(mx, fabsf(f4c(v[k], i)));
+                        if (mx > 0.f) atomicMax(&sMax[side][qd.tc0 + i], __float_as_uint(mx));
+                    }
                 }
             }
-        }
-        __syncthreads();
-        // window exponents and the update of the running references
-        if (tid < 2 * kST) {
-            const int side = tid / kST, c = tid % kST;
-            if (side == 0 || !share) {
-                const float mx = __uint_as_float(sMax[side][c]);
+            // ---- the metadata slot is free once the epilogue of item il - 2 is done
+            if (tid == 0 && !mbar_wait(smem_u32(&bMEmpty[slot]), ((il >> 1) & 1) ^ 1, kWaitLimitNs)) sFail = 1;
+            group_sync(kBarProd, kProdThreads);
+            if (sFail) break;
+            // ---- item exponents: |x| < 2^E; x 2^-E = (x f1) f2 without underflow --
+            if (tab) {
+                const int sd = SAME ? 0 : side_t;
+                const float mx = __uint_as_float(sMax[sd][c_t]);
                 const int E = mx > 0.f ? ilogbf(mx) + 1 : kNone;
-                const int R = sR[side][c];
-                const int newR = E > R ? E : R;
-                sDR[side][c] = (R == kNone) ? 0 : min(newR - R, 63);
-                sDW[side][c] = (E == kNone) ? 63 : min(newR - E, 63);
-                sR[side][c] = newR;
-                const int e = (E == kNone) ? 0 : E;
-                sF1[side][c] = pow2f(-(e >> 1));
-                sF2[side][c] = pow2f(-(e - (e >> 1)));
-            }
-        }
-        __syncthreads();
-
-        // ---- pass 2: chunks of 64 rows, sliced into the staging buffers, MMAs ----
-        bool first = true;
-        for (int c0 = w0; c0 < w1; c0 += kKC, ++chunk_no) {
-            const int b = nbuf == 2 ? (chunk_no & 1) : 0;
-            // the buffer is free once the MMAs of its previous chunk are done
-            if (pending[b]) {
-                if (tid == 0 && !mbar_wait(smem_u32(&sBar[b]), phase[b], kWaitLimitNs)) sFail = 1;
-                phase[b] ^= 1u;
-                pending[b] = false;
-                __syncthreads();
-                if (sFail) break;
-            }
-            unsigned char* bufA = sm + b * kBuf;
-            unsigned char* bufB = share ? bufA : bufA + bytesA;
-            const int c1 = min(w1, c0 + kKC);
-            for (int side = 0; side < (share ? 1 : 2); ++side) {
-                const int wc = side ? wb : wa;
-                const int wpad = side ? N : wa;          // B rows up to N are read by the MMA
-                const float* X = side ? g.B : g.A;
-                unsigned char* base = side ? bufB : bufA;
-                for (int t = tid; t < wpad * 8; t += kThreads) {
-                    const int c = t % wpad, j = t / wpad;
-                    float v[8];
-                    const int ci = c < wc ? sCol[side][c] : -1;
-                    load8(X, ci, sOff, gr.n_u, sPref, nrb, c0 + 8 * j, c1, v);
-                    const float f1 = sF1[side][c], f2 = sF2[side][c];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) v[i] *= f1;
-                    if constexpr (NAT) slice_store_nat(base, c, j, f2, v);
-                    else slice_store<(SA > SB ? SA : SB)>(base, c, j, f2, v);
+                const int e = E == kNone ? 0 : E;
+                if (side_t == sd) {
+                    sF1[side_t][c_t] = pow2f(-(e >> 1));
+                    sF2[side_t][c_t] = pow2f(-(e - (e >> 1)));
                 }
+                const int col = (side_t ? ig.ni : ig.mi) * kST + c_t;
+                sMeta[slot].E[side_t][c_t] = E;
+                sMeta[slot].gcol[side_t][c_t] = c_t < wc_t ? g.col_glob[gr.c_base + col] : -1;
             }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                bool started[NCLS];
+            group_sync(kBarProd, kProdThreads);
+            if (tid == 0) mbar_arrive(smem_u32(&bMFull[slot]));
+            // ---- chunks of 64 rows: load, normalise, slice into a ring stage -------
+            for (int j = 0; j < ig.nchunks; ++j, ++chunk_no) {
+                const int stage = NST == 2 ? (chunk_no & 1) : 0;
+                const int use = NST == 2 ? (chunk_no >> 1) : chunk_no;
+                if (tid == 0 && !mbar_wait(smem_u32(&bEmpty[stage]), (use & 1) ^ 1, kWaitLimitNs)) sFail = 1;
+                group_sync(kBarProd, kProdThreads);
+                if (sFail) break;
+                unsigned char* bufA = ring + stage * kStage;
+                unsigned char* bufB = SAME ? bufA : bufA + bytesA;
+                const int c0 = it.k0 + kKC * j, c1 = min(it.k1, c0 + kKC);
+                for (int side = 0; side < nsides; ++side) {
+                    const float* X = side ? g.B : g.A;
+                    unsigned char* base = side ? bufB : bufA;
+                    const int nq = sNq[side];
+                    // operand rows beyond the tile's columns are never read back:
+                    // they are left as they are.  Neighbouring threads take the
+                    // eight 8-row groups of a quad, so that the 16-byte slice
+                    // stores of a warp land in all eight chunk positions of the
+                    // swizzled rows (no bank conflicts).
+                    for (int t = tid; t < nq * 8; t += kProdThreads) {
+                        const Quad qd = quad_unpack(sQuad[side][t >> 3]);
+                        const int jj = t & 7;
+                        float4 v[8];
+                        load8q(X, qd.u, qd.a0, qd.ld, sOff, gr.n_u, sPref, ig.nrb, c0 + 8 * jj, c1, v);
 #pragma unroll
-                for (int k = 0; k < NCLS; ++k) started[k] = !first;
-                const uint32_t a0 = smem_u32(bufA), b0 = smem_u32(bufB);
+                        for (int i = 0; i < 4; ++i) {
+                            if (!((qd.mask >> i) & 1)) continue;
+                            const int tc = qd.tc0 + i;
+                            const float f1 = sF1[side][tc], f2 = sF2[side][tc];
+                            float x[8];
 #pragma unroll
-                for (int s = 1; s <= SA; ++s)
-#pragma unroll
-                    for (int t = 1; t <= SB; ++t) {
-                        if (s + t > LMAX) continue;
-                        const int cls = level_class<NCLS>(s + t);
-                        const uint32_t d = tmem + (uint32_t)(cls * kST);
-#pragma unroll
-                        for (int kk = 0; kk < kKC / 16; ++kk) {
-                            mma_bf16(d, sw128_desc(a0 + (s - 1) * kPanel + 32 * kk),
-                                     sw128_desc(b0 + (t - 1) * kPanel + 32 * kk), idesc, started[cls] ? 1u : 0u);
-                            started[cls] = true;
+                            for (int k = 0; k < 8; ++k) x[k] = f4c(v[k], i) * f1;
+                            if constexpr (NAT) slice_store_nat(base, tc, jj, f2, x);
+                            else slice_store<(SA > SB ? SA : SB)>(base, tc, jj, f2, x);
                         }
                     }
-                mma_commit(smem_u32(&sBar[b]));
+                }
+                fence_async_smem();
+                group_sync(kBarProd, kProdThreads);
+                if (tid == 0) mbar_arrive(smem_u32(&bFull[stage]));
             }
-            pending[b] = true;
-            first = false;
+            if (sFail) break;
         }
-        // ---- window done: wait for its MMAs, then fold the class sums into acc ------
-        for (int b = 0; b < 2; ++b)
-            if (pending[b]) {
-                if (tid == 0 && !mbar_wait(smem_u32(&sBar[b]), phase[b], kWaitLimitNs)) sFail = 1;
-                phase[b] ^= 1u;
-                pending[b] = false;
+    } else if (warp < kMmaWarp) {
+        // ======================= epilogue ========================================
+        const int ew = warp - kProdWarps;                 // 0..7
+        const int quad = ew & 3;                          // tensor-memory lanes 32 quad .. + 31
+        const int m = 32 * quad + lane;                   // tile row (A column) of this thread
+        const int nhalf = ew >> 2;                        // tile columns [64 nhalf, 64 nhalf + 64)
+        const int etid = tid - kProdThreads;
+        for (int64_t item = blockIdx.x, il = 0; item < g.n_items; item += gridDim.x, ++il) {
+            const GramTcItem it = g.items[item];
+            const GramTcGroup gr = g.groups[it.group];
+            const ItemGeo ig = item_geo<SYM, SAME, ROWS>(it, gr);
+            if (!ig.ok) continue;
+            const int set = (int)(il % NSETS), slot = (int)(il & 1);
+            if (etid == 0) {
+                if (!mbar_wait(smem_u32(&bTFull[set]), (uint32_t)((il / NSETS) & 1), kWaitLimitNs) ||
+                    !mbar_wait(smem_u32(&bMFull[slot]), (uint32_t)((il >> 1) & 1), kWaitLimitNs))
+                    sFail = 1;
             }
-        __syncthreads();
-        if (sFail) break;
-        tc_fence_after();
-        if (flush_act) {
-            const int dRa = sDR[0][m], dWa = sDW[0][m];
-            const int bs = share ? 0 : 1;
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
+            group_sync(kBarEpi, kEpiThreads);
+            if (sFail) break;
+            tc_fence_after();
+            const ItemMeta& mt = sMeta[slot];
+            const int gm = mt.gcol[0][m], Ea = mt.E[0][m];
+            const uint32_t tbase = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(set * NCLS * kST);
+#pragma unroll 1
+            for (int h = 0; h < kST / 16; ++h) {
+                const int n0 = 64 * nhalf + 8 * h;
+                // warp-uniform skips: lanes beyond the tile's A columns, columns
+                // beyond N, or wholly below the diagonal of a diagonal tile
+                if (32 * quad >= ig.wa || n0 >= ig.N || (ig.diag && n0 + 7 < 32 * quad)) continue;
                 float cv[NCLS][8];
-                const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * q + 8 * h);
 #pragma unroll
-                for (int k = 0; k < NCLS; ++k) tmem_load8(ta + (uint32_t)(k * kST), cv[k]);
+                for (int k = 0; k < NCLS; ++k) tmem_load8(tbase + (uint32_t)(k * kST + n0), cv[k]);
+                if (gm < 0 || Ea == kNone) continue;
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const int n = 32 * q + 8 * h + i;
+                    const int n = n0 + i;
+                    const int gn = mt.gcol[1][n], Eb = mt.E[1][n];
+                    if (gn < 0 || Eb == kNone || (ig.diag && m > n)) continue;
                     float cc[NCLS];
 #pragma unroll
                     for (int k = 0; k < NCLS; ++k) cc[k] = cv[k][i];
-                    const long long t = window_value<NCLS>(cc);
-                    const int dR = min(dRa + sDR[bs][n], 63), dW = min(dWa + sDW[bs][n], 63);
-                    acc[8 * h + i] = (acc[8 * h + i] >> dR) + (t >> dW);
+                    const double val = i64_scaled_to_double(window_value<NCLS, U>(cc), Ea + Eb - U);
+                    if (val == 0.0) continue;
+                    atomicAdd(&g.G[(int64_t)gm * g.n_cols + gn], val);
+                    if (SYM && gm != gn) atomicAdd(&g.G[(int64_t)gn * g.n_cols + gm], val);
                 }
             }
-        }
-        tc_fence_before();
-        __syncthreads();                       // tensor memory free for the next window
-    }
-
-    // ---- epilogue: int64 -> FP64, one atomic per element (and its mirror) -------------
-    if (!sFail && tables_ok && flush_act) {
-        const int bs = share ? 0 : 1;
-        const int gm = sGcol[0][m];
-        const int Ra = sR[0][m];
-        if (gm >= 0 && Ra != kNone) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int n = 32 * q + j;
-                const int gn = sGcol[bs][n];
-                if (gn < 0 || (diag && m > n)) continue;
-                const int Rb = sR[bs][n];
-                if (Rb == kNone) continue;
-                const double val = i64_scaled_to_double(acc[j], Ra + Rb - U);
-                if (val == 0.0) continue;
-                atomicAdd(&g.G[(int64_t)gm * g.n_cols + gn], val);
-                if (SYM && gm != gn) atomicAdd(&g.G[(int64_t)gn * g.n_cols + gm], val);
+            tc_fence_before();
+            group_sync(kBarEpi, kEpiThreads);                 // the accumulators and the metadata are read
+            if (etid == 0) {
+                mbar_arrive(smem_u32(&bTEmpty[set]));
+                mbar_arrive(smem_u32(&bMEmpty[slot]));
             }
         }
+    } else {
+        // ======================= MMA issuer (one lane) ===========================
+        int chunk_no = 0;
+        uint32_t last_bar = 0, last_parity = 0;
+        bool issued = false;
+        for (int64_t item = blockIdx.x, il = 0; item < g.n_items; item += gridDim.x, ++il) {
+            const GramTcItem it = g.items[item];
+            const GramTcGroup gr = g.groups[it.group];
+            const ItemGeo ig = item_geo<SYM, SAME, ROWS>(it, gr);
+            if (!ig.ok) continue;
+            const int set = (int)(il % NSETS);
+            bool fail = false;
+            if (lane == 0) {
+                fail = !mbar_wait(smem_u32(&bTEmpty[set]), (uint32_t)(((il / NSETS) & 1) ^ 1), kWaitLimitNs);
+                if (!fail) tc_fence_after();
+                const uint32_t idesc = bf16_idesc(128, ig.N);
+                const uint32_t dset = tmem + (uint32_t)(set * NCLS * kST);
+                bool started[NCLS];
+#pragma unroll
+                for (int k = 0; k < NCLS; ++k) started[k] = false;
+                for (int j = 0; j < ig.nchunks && !fail; ++j, ++chunk_no) {
+                    const int stage = NST == 2 ? (chunk_no & 1) : 0;
+                    const int use = NST == 2 ? (chunk_no >> 1) : chunk_no;
+                    if (!mbar_wait(smem_u32(&bFull[stage]), (uint32_t)(use & 1), kWaitLimitNs)) {
+                        fail = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(ring + stage * kStage);
+                    const uint32_t b0 = SAME ? a0 : a0 + bytesA;
+#pragma unroll
+                    for (int s = 1; s <= SA; ++s)
+#pragma unroll
+                        for (int t = 1; t <= SB; ++t) {
+                            if (s + t > LMAX) continue;
+                            const int cls = level_class<NCLS>(s + t);
+#pragma unroll
+                            for (int kk = 0; kk < kKC / 16; ++kk) {
+                                // the first product of each class in the item starts its sum
+                                mma_bf16(dset + (uint32_t)(cls * kST), sw128_desc(a0 + (s - 1) * kPanel + 32 * kk),
+                                         sw128_desc(b0 + (t - 1) * kPanel + 32 * kk), idesc, started[cls] ? 1u : 0u);
+                                started[cls] = true;
+                            }
+                        }
+                    mma_commit(smem_u32(&bEmpty[stage]));
+                    last_bar = smem_u32(&bEmpty[stage]);
+                    last_parity = (uint32_t)(use & 1);
+                    issued = true;
+                }
+                if (!fail) {
+                    mma_commit(smem_u32(&bTFull[set]));
+                    last_bar = smem_u32(&bTFull[set]);
+                    last_parity = (uint32_t)((il / NSETS) & 1);
+                }
+                if (fail) sFail = 1;
+            }
+            __syncwarp();
+            if (sFail) break;
+        }
+        // after a failure, let the MMAs in flight finish before the tensor
+        // memory is freed
+        if (lane == 0 && sFail && issued) mbar_wait(last_bar, last_parity, kWaitLimitNs);
+        __syncwarp();
     }
 
-    // ---- teardown: after a time-out, give the MMAs in flight one more bounded
-    // wait; then release the tensor memory ----------------------------------------
-    if (sFail && tid == 0) {
-        if (g.status) atomicExch(g.status, kDevTimeout);
-        for (int b = 0; b < 2; ++b)
-            if (pending[b]) mbar_wait(smem_u32(&sBar[b]), phase[b], kWaitLimitNs);
-    }
+    if (sFail && tid == 0 && g.status) atomicExch(g.status, kDevTimeout);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
 }
 
-template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, int KX, bool NAT>
+template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS>
 cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
+    constexpr int smem = 2 * kStage + 1024;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, KX, NAT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn);
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, KX, NAT><<<(unsigned)g.n_items, kThreads, kSmemDyn, s>>>(g);
+    if (g.n_items == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<int64_t>(g.n_items, (int64_t)sms);
+    gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS><<<grid, kThreads, smem, s>>>(g);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_gram_tc(const GramTcArgs& g, GramMode mode, cudaStream_t s) {
-    if (g.n_items == 0) return cudaSuccess;
-    // P^T P: 5 fixed-grid slices, levels <= 6, four level classes, windows of
-    // 192 rows; P^T Y: 3 slices (the lower two natural bf16), levels <= 4, two
-    // classes, windows of 256 rows.  The symmetric modes take the tiles
+    // P^T P: 5 fixed-grid slices, levels <= 6, four level classes; the
+    // diagonal tiles (listed first, n_items_diag of them) stage one panel,
+    // the off-diagonal ones (groups wider than 128 columns) two panels in a
+    // single 192 KB stage.  P^T Y: 3 slices (the lower two natural bf16),
+    // levels <= 4, two classes.  The symmetric modes take the tiles
     // mi <= ni only and mirror them.
     switch (mode) {
-        case GramMode::PtP: return launch_tc<5, 5, 6, 4, true, true, 192, false>(g, s);
-        case GramMode::PtYSym: return launch_tc<3, 3, 4, 2, true, false, 256, true>(g, s);
-        default: return launch_tc<3, 3, 4, 2, false, false, 256, true>(g, s);
+        case GramMode::PtP: {
+            GramTcArgs d = g, o = g;
+            d.n_items = g.n_items_diag;
+            o.items = g.items + g.n_items_diag;
+            o.n_items = g.n_items - g.n_items_diag;
+            cudaError_t e = launch_tc<5, 5, 6, 4, true, true, false, 2, kItemRowsPP>(d, s);
+            if (e != cudaSuccess) return e;
+            return launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP>(o, s);
+        }
+        case GramMode::PtYSym: return launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY>(g, s);
+        default: return launch_tc<3, 3, 4, 2, false, false, true, 2, kItemRowsPY>(g, s);
     }
 }
 
 int gram_tc_tile() { return kST; }
-int gram_tc_split_rows() { return 1024; }
+int gram_tc_item_rows(bool pp) { return pp ? kItemRowsPP : kItemRowsPY; }
 
 }  // namespace femf

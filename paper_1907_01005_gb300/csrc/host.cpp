@@ -188,7 +188,9 @@ struct fe_bcsr {
     std::vector<GramItem> i_py, i_pp;
     // tensor-core Gram (FE_F32)
     std::vector<GramTcGroup> tc_groups;
-    std::vector<GramTcItem> tc_py, tc_pp;
+    // items of P^T Y, its symmetric form, and P^T P (the n_pp_diag diagonal tiles first)
+    std::vector<GramTcItem> tc_py, tc_ps, tc_pp;
+    int64_t n_pp_diag = 0;
     std::vector<int64_t> tc_uoff;
     std::vector<int32_t> tc_cinfo, tc_cglob, tc_rows;
     // post-multiplication and trace (mmult.cu)
@@ -198,7 +200,7 @@ struct fe_bcsr {
     size_t off_rowptr = 0, off_colidx = 0, off_blkoff = 0, off_blockrb = 0, off_rbrows = 0, off_mmitems = 0;
     size_t off_ucol0 = 0, off_rbunion = 0, off_xround = 0;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
-    size_t off_tcg = 0, off_tcpy = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
+    size_t off_tcg = 0, off_tcpy = 0, off_tcps = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
     size_t off_units = 0, off_ld = 0, off_ticket = 0, sync_bytes = 0, off_ucnt = 0, off_tcnt = 0;
     // work items of the apply per patch (by patch id px + npx (py + npy pz)):
     // packed units (p <= 2 and the cell-matrix form) and tiles (p >= 3)
@@ -749,7 +751,10 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                         const int64_t rows = (int64_t)(ex ? 1 : n3[0]) * (ey ? 1 : n3[1]) * (ez ? 1 : n3[2]);
                         if (h * (int64_t)b->elem() / 16 >= (int64_t)INT32_MAX) throw std::bad_alloc();
                         b->hslot[(size_t)k * 8 + e] = int32_t(h * (int64_t)b->elem() / 16);
-                        h += rows * b->ld[b->col_idx[k]];   // a multiple of 16 bytes
+                        // slots start on 128-byte lines: the owner discards them
+                        // from L2 once read, without touching a neighbour's slot
+                        const int64_t per_line = 128 / (int64_t)b->elem();
+                        h += (rows * b->ld[b->col_idx[k]] + per_line - 1) / per_line * per_line;
                     }
             }
             b->halo_elems = h;
@@ -836,6 +841,19 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         }
         if ((int64_t)b->n_values * (int64_t)b->elem() / 16 >= (int64_t)INT32_MAX)
             throw std::bad_alloc();   // offsets in 16-byte units must fit in int32
+        // work order of the apply: the kernels take units and tiles from the
+        // end of the list, so sort by ascending anti-diagonal plane
+        // px + py + pz (stable: patch rank within a plane, a patch's units
+        // together).  A patch's upper neighbours lie in later planes, are
+        // taken a whole plane earlier, and have written their halos long
+        // before the patch needs them.
+        {
+            auto plane = [](int32_t pxyz) { return (pxyz & 1023) + ((pxyz >> 10) & 1023) + (pxyz >> 20); };
+            std::stable_sort(b->units.begin(), b->units.end(),
+                             [&](const Unit& a2, const Unit& b2) { return plane(a2.pxyz) < plane(b2.pxyz); });
+            std::stable_sort(b->tiles.begin(), b->tiles.end(),
+                             [&](const Tile& a2, const Tile& b2) { return plane(a2.pxyz) < plane(b2.pxyz); });
+        }
         b->ucount.assign(R, 0);
         b->tcount.assign(R, 0);
         for (const Unit& u : b->units) {
@@ -876,6 +894,7 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
             }
         if (dtype == FE_F32) {
             // ---- tensor-core Gram: groups of consecutive row blocks ----------
+            std::vector<GramTcItem> pp_off;      // off-diagonal tiles of the symmetric products
             for (int r = 0; r < m->n_patches;) {
                 GramTcGroup gr{};
                 gr.r0 = r;
@@ -921,18 +940,51 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                 if (width > 0) {
                     const int gidx = (int)b->tc_groups.size();
                     const int nt = (width + gram_tc_tile() - 1) / gram_tc_tile();
-                    const int split = gram_tc_split_rows();
-                    for (int mi = 0; mi < nt; ++mi)
-                        for (int ni = 0; ni < nt; ++ni)
-                            for (int k0 = 0; k0 < gr.k_rows; k0 += split) {
-                                const GramTcItem item{gidx, mi | (ni << 16), k0, std::min(gr.k_rows, k0 + split)};
-                                b->tc_py.push_back(item);
-                                if (mi <= ni) b->tc_pp.push_back(item);
-                            }
+                    // the group's rows in near-equal items of at most
+                    // gram_tc_item_rows() (P^T P: fewer rows, for its exact level 4)
+                    for (int pp = 0; pp < 2; ++pp) {
+                        const int nwin = (gr.k_rows + gram_tc_item_rows(pp) - 1) / gram_tc_item_rows(pp);
+                        for (int mi = 0; mi < nt; ++mi)
+                            for (int ni = 0; ni < nt; ++ni)
+                                for (int w = 0; w < nwin; ++w) {
+                                    const int k0 = int((int64_t)gr.k_rows * w / nwin);
+                                    const int k1 = int((int64_t)gr.k_rows * (w + 1) / nwin);
+                                    const GramTcItem item{gidx, mi | (ni << 16), k0, k1};
+                                    if (!pp) {
+                                        b->tc_py.push_back(item);
+                                        if (mi <= ni) b->tc_ps.push_back(item);
+                                    } else if (mi == ni) {
+                                        b->tc_pp.push_back(item);       // diagonal tiles first
+                                    } else if (mi < ni) {
+                                        pp_off.push_back(item);
+                                    }
+                                }
+                    }
                     b->tc_groups.push_back(gr);
                 }
                 r = r1;
             }
+            // window-major order: the row windows of one group (which add into
+            // the same entries of G) are far apart in the list, so CTAs working
+            // at the same time rarely hit the same addresses with their atomics
+            auto window_major = [&](std::vector<GramTcItem>& v, size_t from, size_t to) {
+                std::vector<int> wi(to - from);
+                for (size_t i = from; i < to; ++i)
+                    wi[i - from] = (i > from && v[i - 1].group == v[i].group && v[i - 1].tile == v[i].tile)
+                                       ? wi[i - from - 1] + 1 : 0;
+                std::vector<size_t> idx(to - from);
+                std::iota(idx.begin(), idx.end(), size_t(0));
+                std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b2) { return wi[a] < wi[b2]; });
+                std::vector<GramTcItem> out(to - from);
+                for (size_t i = 0; i < idx.size(); ++i) out[i] = v[from + idx[i]];
+                std::copy(out.begin(), out.end(), v.begin() + from);
+            };
+            window_major(b->tc_py, 0, b->tc_py.size());
+            window_major(b->tc_ps, 0, b->tc_ps.size());
+            window_major(b->tc_pp, 0, b->tc_pp.size());
+            window_major(pp_off, 0, pp_off.size());
+            b->n_pp_diag = (int64_t)b->tc_pp.size();
+            b->tc_pp.insert(b->tc_pp.end(), pp_off.begin(), pp_off.end());
             b->tc_rows.resize(R);
             for (int rr = 0; rr < R; ++rr) b->tc_rows[rr] = int32_t(m->rb_ptr[rr + 1] - m->rb_ptr[rr]);
         }
@@ -967,6 +1019,7 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_tcg = off;   off = align_up(off + b->tc_groups.size() * sizeof(GramTcGroup), 256);
         b->off_tcpy = off;  off = align_up(off + b->tc_py.size() * sizeof(GramTcItem), 256);
         b->off_tcpp = off;  off = align_up(off + b->tc_pp.size() * sizeof(GramTcItem), 256);
+        b->off_tcps = off;  off = align_up(off + b->tc_ps.size() * sizeof(GramTcItem), 256);
         b->off_tcu = off;   off = align_up(off + b->tc_uoff.size() * sizeof(int64_t), 256);
         b->off_tcci = off;  off = align_up(off + b->tc_cinfo.size() * sizeof(int32_t), 256);
         b->off_tccg = off;  off = align_up(off + b->tc_cglob.size() * sizeof(int32_t), 256);
@@ -1055,6 +1108,7 @@ int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
         FE_TRY_CUDA(put(b->off_tcg, b->tc_groups.data(), b->tc_groups.size() * sizeof(GramTcGroup)), "fe_bcsr_bind: groups");
         FE_TRY_CUDA(put(b->off_tcpy, b->tc_py.data(), b->tc_py.size() * sizeof(GramTcItem)), "fe_bcsr_bind: tc items");
         FE_TRY_CUDA(put(b->off_tcpp, b->tc_pp.data(), b->tc_pp.size() * sizeof(GramTcItem)), "fe_bcsr_bind: tc items");
+        FE_TRY_CUDA(put(b->off_tcps, b->tc_ps.data(), b->tc_ps.size() * sizeof(GramTcItem)), "fe_bcsr_bind: tc items");
         FE_TRY_CUDA(put(b->off_tcu, b->tc_uoff.data(), b->tc_uoff.size() * sizeof(int64_t)), "fe_bcsr_bind: union offsets");
         FE_TRY_CUDA(put(b->off_tcci, b->tc_cinfo.data(), b->tc_cinfo.size() * sizeof(int32_t)), "fe_bcsr_bind: column info");
         FE_TRY_CUDA(put(b->off_tccg, b->tc_cglob.data(), b->tc_cglob.size() * sizeof(int32_t)), "fe_bcsr_bind: column ids");
@@ -1207,8 +1261,10 @@ int gram_tc_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaSt
     g.A = static_cast<const float*>(A->values);
     g.B = static_cast<const float*>(B->values);
     g.groups = reinterpret_cast<const GramTcGroup*>(t + A->off_tcg);
-    g.items = reinterpret_cast<const GramTcItem*>(t + (sym ? A->off_tcpp : A->off_tcpy));
-    g.n_items = (int64_t)(sym ? A->tc_pp.size() : A->tc_py.size());
+    const bool pp = sym && A == B;
+    g.items = reinterpret_cast<const GramTcItem*>(t + (pp ? A->off_tcpp : sym ? A->off_tcps : A->off_tcpy));
+    g.n_items = (int64_t)(pp ? A->tc_pp.size() : sym ? A->tc_ps.size() : A->tc_py.size());
+    g.n_items_diag = pp ? A->n_pp_diag : 0;
     g.union_off = reinterpret_cast<const int64_t*>(t + A->off_tcu);
     g.col_info = reinterpret_cast<const int32_t*>(t + A->off_tcci);
     g.col_glob = reinterpret_cast<const int32_t*>(t + A->off_tccg);

@@ -162,6 +162,26 @@ __device__ __forceinline__ void put_own_row(T* yd, const T* ys, int ld, bool zer
     }
 }
 
+// Drops from L2, without a write-back, the halo slots of an own block once
+// all of them are read (no one reads them again before the next apply
+// rewrites them): slot e holds (2p + [px == 0]) ... rows over the directions
+// with e_d = 0, of ld elements; thread t of nt takes every nt-th 128-byte
+// line.  The slots start on 128-byte lines (host layout).
+template <int P, typename T>
+__device__ __forceinline__ void discard_halo(const T* halo, const int32_t* hin, int ld, int px, int py, int pz,
+                                             int t, int nt) {
+    constexpr int Q = 2 * P;
+#pragma unroll 1
+    for (int e = 1; e < 8; ++e) {
+        if (hin[e] < 0) continue;
+        const int rows = ((e & 1) ? 1 : Q + (px == 0)) * ((e & 2) ? 1 : Q + (py == 0)) * ((e & 4) ? 1 : Q + (pz == 0));
+        const int lines = (int)(((int64_t)rows * ld * (int)sizeof(T) + 127) / 128);
+        const char* base = reinterpret_cast<const char*>(halo) + (int64_t)hin[e] * 16;
+        for (int l = t; l < lines; l += nt)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(base + 128 * (int64_t)l) : "memory");
+    }
+}
+
 // Sums the results of the eight cells of a patch in a fixed order and stores
 // every patch node once, for CTAs of 256 threads where thread (cell =
 // tid / 32, lane = tid % 32) holds t, its cell's (p+1)^3 results for one
