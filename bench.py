@@ -40,14 +40,16 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-p4", action="store_true", help="skip the p = 4 workload beside p = 2")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
-    ap.add_argument("--serving", type=int, default=200, help="requests in the serving run (0: skip)")
-    ap.add_argument("--serving-pool", type=int, default=8, help="distinct workloads in the serving mix")
-    ap.add_argument("--serving-full", action="store_true",
-                    help="draw serving meshes up to 64x40x40 and 640 orbitals (slow host set-up)")
+    ap.add_argument("--serving", type=int, default=2000, help="requests per load point of the serving run (0: skip)")
+    ap.add_argument("--serving-pool", type=int, default=6, help="distinct workloads in the serving mix")
+    ap.add_argument("--serving-small", dest="serving_full", action="store_false",
+                    help="draw serving meshes from the two smaller sizes and 32-320 orbitals only")
     ap.add_argument("--serving-loads", type=lambda s: [float(x) for x in s.split(",")], default=[0.5, 0.8, 1.2, 2.0],
                     help="offered loads, as multiples of the one-at-a-time rate (comma-separated)")
-    ap.add_argument("--cpu-blocks", type=int, default=8, help="column blocks in the CPU oracle sample")
+    ap.add_argument("--cpu-blocks", type=int, default=1000,
+                    help="column blocks in the CPU oracle sample (default: all of them)")
     return ap.parse_args()
 
 
@@ -145,18 +147,19 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(cfg, n_blocks, fp32=True):
-    """Times the FP64 oracle (assembled SpMM restricted to the pattern, then
-    P^T Y and P^T P) on the first `n_blocks` column blocks of the workload.
-    Assembly of the rows it needs is timed separately."""
+def _oracle_worker(cfg_name, pick, fp32, conn):
+    """One CPU worker of the oracle team: sets up the FP64 oracle (assembled
+    operator on the rows of its column blocks' pattern, the orbitals of its
+    column blocks) once, then on each "go" times Y = mask(P) (H P), P^T Y and
+    P^T P for its columns and sends the seconds back."""
     import numpy as np
     from oracle import fe_oracle as O
     from synth import inputs
+    cfg = inputs.get_config(cfg_name)
     mesh = O.BoxMesh.from_config(cfg)
     blk = O.Blocking(mesh)
     centres = inputs.orbital_centres(cfg)
     perm, ptr = O.column_blocks(blk, centres, cfg.n_col_blocks)
-    pick = list(range(min(n_blocks, len(ptr) - 1)))
     orbs = {int(perm[j]) for c in pick for j in range(ptr[c], ptr[c + 1])}
     mv = O.build_orbitals(mesh, cfg, centres, round_fp32=fp32, orbitals=orbs)
     pat = O.block_pattern(blk, mv, perm, ptr)
@@ -168,17 +171,88 @@ def oracle_sample(cfg, n_blocks, fp32=True):
     H = O.assemble(mesh, O.potential_fn(cfg, fp32), cells=cells)
     t_asm = time.perf_counter() - t0
     Psp = O.sparse_multivector(mesh, mv)
-    t0 = time.perf_counter()
-    Y = O.apply_masked(H, Psp, blk, pat, cb_of_orb)
-    O.gram(Psp, Y)
-    O.gram(Psp, Psp)
-    t_run = time.perf_counter() - t0
-    ncols = len(orbs)
-    return {"value": mesh.n_nodes * ncols / t_run, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {len(pick)} of {len(ptr) - 1} column blocks ({ncols} of {len(perm)} "
-                      f"columns), all their pattern rows; FP64 scipy SpMM + Gram; assembly of the "
-                      f"needed rows ({len(cells)} cells) timed apart: {t_asm:.2f} s",
-            "seconds": t_run, "assembly_s": t_asm}
+    conn.send(("ready", len(orbs), t_asm, len(cells), int(mesh.n_nodes), len(ptr) - 1, len(perm)))
+    while conn.recv() == "go":
+        t0 = time.perf_counter()
+        Y = O.apply_masked(H, Psp, blk, pat, cb_of_orb)
+        O.gram(Psp, Y)
+        O.gram(Psp, Psp)
+        conn.send(time.perf_counter() - t0)
+
+
+class OracleTeam:
+    """The FP64 oracle as it stands, run on the host cores: one spawned
+    worker process per core in the affinity mask (at most one per column
+    block), each with a contiguous share of the sampled column blocks.  A
+    step sends "go" to every worker and waits for all of them, so the
+    workers run concurrently and the step's wall time covers all sampled
+    columns.  Assembly is done once per worker at start-up and timed apart."""
+
+    def __init__(self, cfg, blocks, workers=None, fp32=True):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        n = max(1, min(workers or cores, len(blocks)))
+        self.cores_available = cores
+        shares = [blocks[i * len(blocks) // n:(i + 1) * len(blocks) // n] for i in range(n)]
+        self.conns, self.procs = [], []
+        t0 = time.perf_counter()
+        for share in shares:
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(cfg.name, share, fp32, b), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        info = [c.recv() for c in self.conns]
+        self.setup_s = time.perf_counter() - t0
+        self.cols = [x[1] for x in info]
+        self.assembly_s = max(x[2] for x in info)
+        self.n_nodes = info[0][4]
+        self.n_blocks_total, self.n_cols_total = info[0][5], info[0][6]
+        self.blocks = blocks
+        self.workers = n
+
+    def step(self, only=None):
+        """Seconds of one step of all workers (or of worker `only` alone)."""
+        sel = range(self.workers) if only is None else [only]
+        t0 = time.perf_counter()
+        for i in sel:
+            self.conns[i].send("go")
+        for i in sel:
+            self.conns[i].recv()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for c in self.conns:
+            c.send("stop")
+        for p in self.procs:
+            p.join(timeout=30)
+
+    def sample_text(self):
+        nb = len(self.blocks)
+        scope = ("all" if nb == self.n_blocks_total else f"{nb} of") + f" {self.n_blocks_total} column blocks"
+        return (f"{scope} ({sum(self.cols)} of {self.n_cols_total} columns), all their pattern rows, "
+                f"split over {self.workers} worker processes; FP64 scipy SpMM + P^T Y + P^T P per "
+                f"worker's columns; assembly of the needed rows timed apart ({self.assembly_s:.1f} s)")
+
+
+def cpu_baseline(cfg, n_blocks, reps=5):
+    """The oracle on all host cores (median of `reps` steps) and, beside it,
+    one worker's share alone (single core)."""
+    team = OracleTeam(cfg, list(range(min(n_blocks, cfg.n_col_blocks))))
+    try:
+        team.step()                                        # warm caches
+        t_all = statistics.median(team.step() for _ in range(reps))
+        t_one = statistics.median(team.step(only=0) for _ in range(reps))
+        cols = sum(team.cols)
+        return {"value": team.n_nodes * cols / t_all, "unit": UNIT, "cores": team.workers, "kind": "oracle",
+                "sample": team.sample_text(), "seconds_median_of": reps, "seconds": t_all,
+                "cores_in_affinity_mask": team.cores_available,
+                "single_core": {"value": team.n_nodes * team.cols[0] / t_one, "seconds": t_one,
+                                "columns": team.cols[0]},
+                "setup_s": team.setup_s}
+    finally:
+        team.close()
 
 
 def run_reference(args):
@@ -186,20 +260,22 @@ def run_reference(args):
         return
     from synth import inputs
     cfg = inputs.get_config(args.config)
-    times, vals = [], []
-    for i in range(args.warmup + args.steps):
-        r = oracle_sample(cfg, 1)
-        if i >= args.warmup:
-            times.append(r["seconds"])
-            vals.append(r["value"])
-    v = statistics.median(vals)
+    team = OracleTeam(cfg, list(range(min(args.cpu_blocks, cfg.n_col_blocks))))
+    try:
+        for _ in range(args.warmup):
+            team.step()
+        times = [team.step() for _ in range(args.steps)]
+    finally:
+        team.close()
+    t = statistics.median(times)
+    v = team.n_nodes * sum(team.cols) / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+            "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": _workload_name(cfg)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": r["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": team.workers, "kind": "oracle",
+                             "sample": team.sample_text()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -303,6 +379,103 @@ def time_path(pb, steps, warmup):
     return total, per
 
 
+def kernel_rooflines(cfg, pb, per, ms_step, hbm_peak, peak_src, fp32_peak):
+    """Per-kernel medians, rooflines and the dominant kernel's roofline from the
+    breakdown timings `per` of one workload."""
+    info = pb.P.info
+    # algorithmic work per launch (stored entries, not the 16-byte row padding):
+    # apply reads P and V_q and writes Y; P^T Y reads P and Y; P^T P reads P
+    s = 4
+    n_q = int(pb.mesh.info.n_q)
+    nnz = int(info.stored_entries)
+    apply_bytes = 2 * nnz * s + n_q * s
+    py_bytes = 2 * nnz * s
+    pp_bytes = nnz * s
+    n = cfg.p + 1
+    apply_flops = info.active_cell_cols * (18 * n ** 4 + 3 * n ** 3)
+    # sliced Gram: 6 bf16 slice products for P^T Y (3 x 3 slices, s+t <= 4)
+    # and 15 for P^T P (5 x 5 slices, s+t <= 6), both on half the output
+    # blocks (symmetric forms: P^T Y on a closed pattern, P^T P)
+    py_tc = (3.0 if pb.P.get_closed() else 6.0) * info.gram_flops
+    pp_tc = 7.5 * info.gram_flops
+    bf16_peak = load_bf16_peak()
+    t_apply = statistics.median(per["apply"]) * 1e-3
+    t_py = statistics.median(per["gram_py"]) * 1e-3
+    t_pp = statistics.median(per["gram_pp"]) * 1e-3
+
+    def bound(t, nbytes, work, peak, unit_name):
+        """roofline of one kernel: the resource whose ideal time is longest"""
+        t_mem = nbytes / (hbm_peak * 1e9)
+        t_cmp = work / peak
+        if t_mem >= t_cmp:
+            return {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": nbytes / t / 1e9 / hbm_peak}
+        return {"bound": unit_name, "achieved": work / t / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": work / t / peak}
+
+    kernels = {
+        "apply": {"ms_p50": 1e3 * t_apply, "ms_p99": pct(per["apply"], 0.99), "bytes": apply_bytes,
+                  "flops": apply_flops, "gbs": apply_bytes / t_apply / 1e9,
+                  "hbm_frac": apply_bytes / t_apply / 1e9 / hbm_peak,
+                  "gflops": apply_flops / t_apply / 1e9, "fp32_frac": apply_flops / t_apply / fp32_peak,
+                  **{"roof_" + k: v for k, v in bound(t_apply, apply_bytes, apply_flops, fp32_peak, "alu").items()}},
+        "gram_py": {"ms_p50": 1e3 * t_py, "ms_p99": pct(per["gram_py"], 0.99), "bytes": py_bytes,
+                    "gflops": info.gram_flops / t_py / 1e9, "tc_tflops": py_tc / t_py / 1e12,
+                    "gbs": py_bytes / t_py / 1e9,
+                    **{"roof_" + k: v for k, v in bound(t_py, py_bytes, py_tc, bf16_peak, "tensor").items()}},
+        "gram_pp": {"ms_p50": 1e3 * t_pp, "ms_p99": pct(per["gram_pp"], 0.99), "bytes": pp_bytes,
+                    "gflops": info.gram_flops / t_pp / 1e9, "tc_tflops": pp_tc / t_pp / 1e12,
+                    "gbs": pp_bytes / t_pp / 1e9,
+                    **{"roof_" + k: v for k, v in bound(t_pp, pp_bytes, pp_tc, bf16_peak, "tensor").items()}},
+    }
+    dom = max(("apply", t_apply), ("gram_py", t_py), ("gram_pp", t_pp), key=lambda x: x[1])[0]
+    kd = kernels[dom]
+    roof = {"kernel": dom, "bound": kd["roof_bound"], "achieved": kd["roof_achieved"], "peak": kd["roof_peak"],
+            "unit": kd["roof_unit"], "frac": kd["roof_frac"],
+            "traffic": ncu_traffic(dom, cfg.name),
+            "peak_source": (f"{peak_src} hbm_gbs" if kd["roof_bound"] == "hbm" else
+                            "measured fp32 FMA probe" if kd["roof_bound"] == "alu" else "measured bf16_tflops"),
+            "per_launch": "achieved = algorithmic bytes (stored entries x 4 B) / CUDA-event median"}
+    step_bytes = apply_bytes + py_bytes + pp_bytes
+    step_roof = {"bytes": step_bytes, "ideal_ms": step_bytes / (hbm_peak * 1e9) * 1e3,
+                 "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak}
+
+    return t_apply, t_py, t_pp, kernels, roof, step_roof
+
+
+def measure_second(cfg_name, args, world, hbm_peak, peak_src, fp32_peak):
+    """The same step on a second workload (the p = 4 paper-scale mesh beside
+    p = 2): step time, per-kernel breakdown and rooflines, value."""
+    import torch
+    from paper_1907_01005_gb300 import FE_F32, harness
+    from synth import inputs
+    cfg = inputs.get_config(cfg_name)
+    pb = harness.build_problem(cfg, FE_F32)
+    harness.to_device(pb)
+    if not args.no_tune:
+        from paper_1907_01005_gb300 import autotune
+        autotune(pb.mesh, pb.P, pb.Y)
+    steps = max(20, args.steps // 4)
+    barrier(world)
+    total_ms, per = time_path(pb, steps, max(3, args.warmup // 2))
+    barrier(world)
+    if pb.mesh.check_device() != 0:
+        raise RuntimeError("device status word set during the timed region")
+    ms_step = max_over_ranks(total_ms / steps, world)
+    N, M = pb.mesh.n_dofs, pb.n_cols
+    t_apply, t_py, t_pp, kernels, roof, step_roof = kernel_rooflines(cfg, pb, per, ms_step, hbm_peak, peak_src,
+                                                                     fp32_peak)
+    out = {"workload": _workload_name(cfg), "steps": steps, "ms_per_step": ms_step,
+           "value": whole_job_value(N, M, ms_step, world), "unit": UNIT,
+           "p50_ms": pct(per["step"], 0.5), "p99_ms": pct(per["step"], 0.99),
+           "sequential_ms_per_step": statistics.median(per["sequential"]),
+           "kernels": kernels, "roofline": roof, "step_hbm_roofline": step_roof,
+           "launch": dict(zip(("persistent", "ctas_per_sm", "cells_per_round"), pb.P.get_launch()))}
+    del pb
+    torch.cuda.empty_cache()
+    return out
+
+
 def time_graph(pb, steps, warmup):
     """ms per step of the CUDA graph of the whole step (one graph launch per step)."""
     import torch
@@ -387,15 +560,22 @@ def time_om(pb, steps):
     return out
 
 
-def serving_run(args, dtype=1):
-    """Poisson stream of apply_H + Gram requests through the continuous-batching
-    server: a pool of distinct workloads drawn from the serving mix, arrivals
-    at 80% of the rate one request at a time would sustain."""
+SIZE_CLASSES = {"small": (0.0, 1e7), "medium": (1e7, 1e8), "large": (1e8, float("inf"))}
+
+
+def serving_run(args, dtype=1, loads=None, n_requests=None):
+    """Poisson streams of apply_H + Gram requests through the continuous-batching
+    server: a pool of distinct workloads drawn from the serving mix (meshes
+    taken in turn), arrivals at multiples of the rate one request at a time
+    sustains; p50/p99 overall and per size class (DoF x columns) beside each
+    class's one-at-a-time latency."""
     from paper_1907_01005_gb300 import harness
     from paper_1907_01005_gb300.serving import Server, latency_stats
     from synth import inputs
     meshes = inputs.SERVING_MESHES if args.serving_full else inputs.SERVING_MESHES[:2]
     orbs = (32, 640) if args.serving_full else (32, 320)
+    loads = loads or args.serving_loads
+    n_requests = n_requests or args.serving
     t0 = time.perf_counter()
     probs = []
     for cfg in inputs.serving_mix(args.serving_pool, meshes=meshes, orb_range=orbs):
@@ -410,32 +590,44 @@ def serving_run(args, dtype=1):
     for pid in pids:                      # residency and one warm call each
         srv.submit(pid)
         srv.drain()
-    t1 = time.perf_counter()
-    for pid in pids:
-        srv.submit(pid)
-        srv.drain()
-    serial = (time.perf_counter() - t1) / len(pids)
+    alone_ms = {}
+    for pid in pids:                      # one at a time: the service time of each payload
+        ts = []
+        for _ in range(3):
+            r = srv.submit(pid)
+            srv.drain()
+            ts.append(r.latency)
+        alone_ms[pid] = 1e3 * statistics.median(ts)
+    serial = sum(alone_ms.values()) / len(pids) * 1e-3
     # offered load swept in multiples of the rate one request at a time
     # sustains; the main figures are those at 0.8 of it
     sweep = []
     st = None
-    for li, load in enumerate(args.serving_loads):
+    for li, load in enumerate(loads):
         rate = load / serial
         rng = np.random.default_rng(190701005 + li)
-        arr = inputs.poisson_arrivals(args.serving, rate, seed=190701005 + li)
-        trace = [(float(arr[i]), int(pids[rng.integers(len(pids))])) for i in range(args.serving)]
+        arr = inputs.poisson_arrivals(n_requests, rate, seed=190701005 + li)
+        trace = [(float(arr[i]), int(pids[rng.integers(len(pids))])) for i in range(n_requests)]
         srv.finished.clear()
         reqs = srv.run_trace(trace)
-        s = latency_stats(reqs, dofs_cols)
+        s = latency_stats(reqs, dofs_cols, SIZE_CLASSES, alone_ms)
         sweep.append({"load": load, "offered_rate_per_s": rate, "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"],
-                      "dof_cols_per_s": s["dof_cols_per_s"], "achieved_rate_per_s": len(reqs) / s["span_s"]})
+                      "dof_cols_per_s": s["dof_cols_per_s"], "achieved_rate_per_s": len(reqs) / s["span_s"],
+                      "classes": s.get("classes", {})})
         if st is None or abs(load - 0.8) < 1e-9:
             st = dict(s, offered_rate_per_s=rate)
     st.update({"sweep": sweep, "serial_ms": 1e3 * serial, "slots": srv.slots, "pool": len(pids),
                "pool_dofs": [int(srv.payloads[p].problem.mesh.n_dofs) for p in pids],
                "pool_columns": [int(srv.payloads[p].problem.n_cols) for p in pids],
                "pool_degree": [int(srv.payloads[p].problem.cfg.p) for p in pids],
-               "evictions": srv.evictions, "host_setup_s": setup_s, "dtype": "f32" if dtype == 1 else "f64"})
+               "alone_ms": [alone_ms[p] for p in pids],
+               "evictions": srv.evictions, "host_setup_s": setup_s, "dtype": "f32" if dtype == 1 else "f64",
+               "serving_config": (f"{n_requests} Poisson requests per load point at {', '.join(f'{x:g}' for x in loads)}"
+                                  f" x the one-at-a-time rate, drawn from a pool of {len(pids)} workloads "
+                                  f"(meshes {', '.join('x'.join(map(str, m)) for m in meshes)} cells in turn, "
+                                  f"p in {{2, 4}}, {orbs[0]}-{orbs[1]} orbitals log-uniform, fill 10-30%); "
+                                  f"4 stream slots; admission by device-memory footprint, shortest predicted "
+                                  f"first with an age bound, last slot kept for small requests")})
     return st
 
 
@@ -481,61 +673,12 @@ def main():
     ms_step = max_over_ranks(total_ms / args.steps, world)
     value = whole_job_value(N, M, ms_step, world)
 
-    # algorithmic work per launch (stored entries, not the 16-byte row padding):
-    # apply reads P and V_q and writes Y; P^T Y reads P and Y; P^T P reads P
+    t_apply, t_py, t_pp, kernels, roof, step_roof = kernel_rooflines(cfg, pb, per, ms_step, hbm_peak, peak_src,
+                                                                     fp32_peak)
     s = 4
-    n_q = int(pb.mesh.info.n_q)
     nnz = int(info.stored_entries)
-    apply_bytes = 2 * nnz * s + n_q * s
-    py_bytes = 2 * nnz * s
-    pp_bytes = nnz * s
-    n = cfg.p + 1
-    apply_flops = info.active_cell_cols * (18 * n ** 4 + 3 * n ** 3)
-    # sliced Gram: 6 bf16 slice products for P^T Y (3 x 3 slices, s+t <= 4),
-    # 15 for P^T P (5 x 5 slices, s+t <= 6) on half the output blocks
-    py_tc = 6 * info.gram_flops
-    pp_tc = 7.5 * info.gram_flops
+    apply_bytes = kernels["apply"]["bytes"]
     bf16_peak = load_bf16_peak()
-    t_apply = statistics.median(per["apply"]) * 1e-3
-    t_py = statistics.median(per["gram_py"]) * 1e-3
-    t_pp = statistics.median(per["gram_pp"]) * 1e-3
-
-    def bound(t, nbytes, work, peak, unit_name):
-        """roofline of one kernel: the resource whose ideal time is longest"""
-        t_mem = nbytes / (hbm_peak * 1e9)
-        t_cmp = work / peak
-        if t_mem >= t_cmp:
-            return {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": nbytes / t / 1e9 / hbm_peak}
-        return {"bound": unit_name, "achieved": work / t / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": work / t / peak}
-
-    kernels = {
-        "apply": {"ms_p50": 1e3 * t_apply, "ms_p99": pct(per["apply"], 0.99), "bytes": apply_bytes,
-                  "flops": apply_flops, "gbs": apply_bytes / t_apply / 1e9,
-                  "hbm_frac": apply_bytes / t_apply / 1e9 / hbm_peak,
-                  "gflops": apply_flops / t_apply / 1e9, "fp32_frac": apply_flops / t_apply / fp32_peak,
-                  **{"roof_" + k: v for k, v in bound(t_apply, apply_bytes, apply_flops, fp32_peak, "alu").items()}},
-        "gram_py": {"ms_p50": 1e3 * t_py, "ms_p99": pct(per["gram_py"], 0.99), "bytes": py_bytes,
-                    "gflops": info.gram_flops / t_py / 1e9, "tc_tflops": py_tc / t_py / 1e12,
-                    "gbs": py_bytes / t_py / 1e9,
-                    **{"roof_" + k: v for k, v in bound(t_py, py_bytes, py_tc, bf16_peak, "tensor").items()}},
-        "gram_pp": {"ms_p50": 1e3 * t_pp, "ms_p99": pct(per["gram_pp"], 0.99), "bytes": pp_bytes,
-                    "gflops": info.gram_flops / t_pp / 1e9, "tc_tflops": pp_tc / t_pp / 1e12,
-                    "gbs": pp_bytes / t_pp / 1e9,
-                    **{"roof_" + k: v for k, v in bound(t_pp, pp_bytes, pp_tc, bf16_peak, "tensor").items()}},
-    }
-    dom = max(("apply", t_apply), ("gram_py", t_py), ("gram_pp", t_pp), key=lambda x: x[1])[0]
-    kd = kernels[dom]
-    roof = {"kernel": dom, "bound": kd["roof_bound"], "achieved": kd["roof_achieved"], "peak": kd["roof_peak"],
-            "unit": kd["roof_unit"], "frac": kd["roof_frac"],
-            "traffic": ncu_traffic(dom, cfg.name),
-            "peak_source": (f"{peak_src} hbm_gbs" if kd["roof_bound"] == "hbm" else
-                            "measured fp32 FMA probe" if kd["roof_bound"] == "alu" else "measured bf16_tflops"),
-            "per_launch": "achieved = algorithmic bytes (stored entries x 4 B) / CUDA-event median"}
-    step_bytes = apply_bytes + py_bytes + pp_bytes
-    step_roof = {"bytes": step_bytes, "ideal_ms": step_bytes / (hbm_peak * 1e9) * 1e3,
-                 "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -556,6 +699,10 @@ def main():
             "alu_peaks_tflops": {"fp32": probe_alu(1) / 1e12, "fp32x2": probe_alu(3) / 1e12,
                                  "fp64": fp64_peak / 1e12},
             "gpu_launches": 3 * args.steps, "clocks": clk}
+
+    # the p = 4 paper-scale workload beside p = 2 (same DoFs and orbitals)
+    if args.config == "p2" and not args.no_p4:
+        line["p4"] = measure_second("p4", args, world, hbm_peak, peak_src, fp32_peak)
 
     # the rest of an orbital-minimisation gradient evaluation (NEXT rows f1, f3)
     om = time_om(pb, max(10, args.steps // 10))
@@ -634,10 +781,10 @@ def main():
         line["serving"] = serving_run(args, 1)
         if not args.no_fp64:
             torch.cuda.empty_cache()
-            line["serving_fp64"] = serving_run(args, 2)
+            line["serving_fp64"] = serving_run(args, 2, loads=[0.8], n_requests=max(1, args.serving // 4))
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(cfg, args.cpu_blocks)
+        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_blocks)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

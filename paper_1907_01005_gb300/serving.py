@@ -7,11 +7,19 @@ matrices resident in device memory while the payload is in use, and evicts
 idle payloads (least recently used first) when the memory budget is needed.
 
 Requests name a payload (and may bring new values of P from host memory).
-They are admitted in arrival order as soon as
+A queued request is admitted as soon as
   * a stream slot is free (at most `slots` requests are on the GPU), and
   * the payload is resident or its device footprint fits in the budget
-    (after evicting idle payloads),
-so requests that arrive while others run join them on the device: each
+    (after evicting idle payloads).
+Among the queued requests the predicted shortest goes first (the prediction
+is a running mean of the payload's observed service time, seeded from its
+DoF x column count), except that a request which has waited more than
+`age_factor` times its own prediction (at least `min_age_s`) is aged and
+goes ahead of all unaged ones, in arrival order, so large requests cannot
+starve.  The last free slot is kept for small requests (predicted at most
+the median of the registered payloads) unless the request is aged, so that
+small requests do not queue behind a GPU full of large ones.  Requests that
+arrive while others run join them on the device: each
 admitted request runs `fe_apply_H_gram` on its own CUDA stream and the
 kernels of different requests overlap.  A request completes when its Gram
 matrices (and, if asked, Y) are back in host memory; its latency is measured
@@ -48,6 +56,7 @@ class Payload:
     host: dict | None = None
     busy: bool = False
     last_used: float = 0.0
+    service_s: float = 0.0        # running estimate of one request's service time
 
     @property
     def dofs_cols(self) -> float:
@@ -81,7 +90,8 @@ class Request:
 class Server:
     """Continuous-batching server on one GPU (see the module docstring)."""
 
-    def __init__(self, budget_bytes: int | None = None, slots: int = 4, device: str = "cuda"):
+    def __init__(self, budget_bytes: int | None = None, slots: int = 4, device: str = "cuda",
+                 age_factor: float = 4.0, min_age_s: float = 2e-3, seed_rate: float = 1e11):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -100,14 +110,25 @@ class Server:
         self.finished: list[Request] = []
         self._next_rid = 0
         self._lock = threading.Lock()
+        self.age_factor = age_factor
+        self.min_age_s = min_age_s
+        self.seed_rate = seed_rate                 # DoF*columns/s that seeds the service estimates
+        self.small_s = 0.0                         # the median service estimate of the payloads
 
     # ---- registration ---------------------------------------------------------
     def register(self, problem: harness.Problem) -> int:
         """Registers a host-built problem (harness.build_problem) as a payload."""
         pid = len(self.payloads)
         key = (id(problem.mesh),)
-        self.payloads[pid] = Payload(pid, problem, key)
+        pl = Payload(pid, problem, key)
+        pl.service_s = pl.dofs_cols / self.seed_rate
+        self.payloads[pid] = pl
+        self._update_small()
         return pid
+
+    def _update_small(self):
+        est = sorted(p.service_s for p in self.payloads.values())
+        self.small_s = est[(len(est) - 1) // 2] if est else 0.0
 
     # ---- memory -----------------------------------------------------------------
     def _mesh_resident(self, pl: Payload) -> int:
@@ -227,20 +248,30 @@ class Server:
                 self.free_streams.append(r.stream)
                 pl.busy = False
                 pl.last_used = r.done
+                pl.service_s = 0.7 * pl.service_s + 0.3 * (r.done - r.admitted)
                 self.finished.append(r)
                 n += 1
+        if n:
+            self._update_small()
         with self._lock:
             pending = list(self.queue)
+        now = time.perf_counter()
+        service = {pid: pl.service_s for pid, pl in self.payloads.items()}
+        order = admission_order(pending, service, now, self.age_factor, self.min_age_s)
         admitted = []
         busy_now = set()
-        for r in pending:
+        for r, old in order:
             if not self.free_streams:
                 break
             pl = self.payloads[r.pid]
             if pl.busy or r.pid in busy_now:
                 continue
+            if not may_take_slot(len(self.free_streams), self.slots, old, pl.service_s, self.small_s):
+                continue                       # the last slot waits for a small or an aged request
             if not self._fits(pl):
-                break                          # keep arrival order once memory is the limit
+                if old:
+                    break                      # memory frees up for the aged request first
+                continue
             self._launch(r)
             admitted.append(r)
             busy_now.add(r.pid)
@@ -279,10 +310,46 @@ class Server:
         return reqs
 
 
-def latency_stats(reqs, dofs_cols) -> dict:
-    """p50/p99 latency (ms) and aggregate DoF*columns/s of finished requests."""
+def admission_order(pending, service_s, now, age_factor, min_age_s):
+    """The order in which queued requests are considered, with their aged
+    flag: a request is aged when it has waited more than age_factor times
+    its payload's predicted service time (and at least min_age_s); aged
+    requests come first in arrival order, then the others by predicted
+    service time (ties by arrival)."""
+    def aged(r):
+        return now - r.arrival > max(age_factor * service_s[r.pid], min_age_s)
+    flagged = [(r, aged(r)) for r in pending]
+    return sorted(flagged, key=lambda x: (0, x[0].arrival, 0.0) if x[1] else (1, service_s[x[0].pid], x[0].arrival))
+
+
+def may_take_slot(free_slots, slots, aged, service_s, small_s):
+    """The last free slot (of more than one) goes to a small request (predicted
+    at most small_s) or to an aged one only."""
+    return not (free_slots == 1 and slots > 1 and not aged and service_s > small_s)
+
+
+def latency_stats(reqs, dofs_cols, classes=None, alone_ms=None) -> dict:
+    """p50/p99 latency (ms) and aggregate DoF*columns/s of finished requests;
+    with `classes` (name -> (low, high) DoF*column bounds) also per size class,
+    beside the class's one-at-a-time latency when `alone_ms` (payload id ->
+    ms) is given."""
     lat = np.array([r.latency for r in reqs]) * 1e3
     span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
     work = float(sum(dofs_cols[r.pid] for r in reqs))
-    return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "dof_cols_per_s": work / span, "span_s": span}
+    out = {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "mean_ms": float(lat.mean()), "dof_cols_per_s": work / span, "span_s": span}
+    if classes:
+        per = {}
+        for name, (lo, hi) in classes.items():
+            sel = [i for i, r in enumerate(reqs) if lo <= dofs_cols[r.pid] < hi]
+            if not sel:
+                continue
+            cl = lat[sel]
+            d = {"requests": len(sel), "p50_ms": float(np.percentile(cl, 50)), "p99_ms": float(np.percentile(cl, 99))}
+            if alone_ms:
+                a = [alone_ms[reqs[i].pid] for i in sel]
+                d["alone_ms_median"] = float(np.median(a))
+                d["p99_over_alone"] = d["p99_ms"] / max(float(np.median(a)), 1e-9)
+            per[name] = d
+        out["classes"] = per
+    return out
