@@ -72,12 +72,18 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
         return;
     }
     __shared__ int64_t sOff[8];
-    __shared__ int32_t sHout[8], sHin[8];
+    __shared__ int32_t sHout[8], sHin[1][8];
+    __shared__ int sHn[1][8], sHb[1][8];              // fetched halo slots: elements, buffer offsets
+    __shared__ int sCol0[1], sLd1[1];                 // the tile's one block: column 0, ld columns
     __shared__ int sNode[NPN];                       // node_entry: row, owner slot, boundary bit, face data
     if (threadIdx.x < 8) {
         sOff[threadIdx.x] = tile.off[threadIdx.x];
         sHout[threadIdx.x] = tile.hout[threadIdx.x];
-        sHin[threadIdx.x] = tile.hin[threadIdx.x];
+        sHin[0][threadIdx.x] = tile.hin[threadIdx.x];
+    }
+    if (threadIdx.x == 0) {
+        sCol0[0] = 0;
+        sLd1[0] = ld;
     }
     for (int n = threadIdx.x; n < NPN; n += blockDim.x)
         sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet, a.npx, a.npy, a.npz);
@@ -295,33 +301,33 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
     if (threadIdx.x < 32 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) &&
         threadIdx.x == 0)
         atomicExch(a.status, kDevTimeout);
-    __syncthreads();
     const int64_t oown = sOff[7];
-    if (oown >= 0) {
-        for (int node = threadIdx.x; node < NPN; node += blockDim.x) {
-            const int ne = sNode[node];
-            if (((ne >> 16) & 7) != 7) continue;
-            const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
-            put_own_row<P>(a.Y + oown + (int64_t)(ne & 0xffff) * ld, Yp + node * ld, ld, (ne & kBoundary) != 0,
-                           (ne >> kAuxShift) & 7, a.halo, sHin, i, j, k, px, py, pz);
-        }
-        __syncthreads();                               // the halo rows addressed to this tile are read
-        if (threadIdx.x < 32) discard_halo<P>(a.halo, sHin, ld, px, py, pz, threadIdx.x, 32);   // one warp
+    // the halos addressed to this tile, fetched into the free gather buffer
+    if (threadIdx.x < 8) {
+        const int e = threadIdx.x;
+        sHn[0][e] = (e > 0 && oown >= 0 && sHin[0][e] >= 0) ? halo_slot_rows<P>(e, px, py, pz) * ld : 0;
     }
+    __syncthreads();
+    fetch_halo(U, a.halo, sHin, sHn, sHb, 1);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    // own rows: own part plus the halo rows, stored once
+    store_own_rows<P>([&](int) -> T* { return oown >= 0 ? a.Y + oown : nullptr; }, Yp, ld, sCol0, sLd1, U, sHb, sHn,
+                      sNode, 1, px, py, pz);
 }
 
 template <typename T, int P>
 cudaError_t launch_p(const ApplyArgs<T>& a, cudaStream_t s) {
     const size_t smem = apply_smem_bytes<T>(P, a.wmax, a.ldmax, a.cells_per_round);
     const int threads = apply_threads<T>(P, a.wmax, a.cells_per_round);
-    // dynamic shared memory up to 224 KB: the node tables take 3 KB of the 227 KB a CTA may use
+    // dynamic shared memory up to 223 KB: the node and halo tables take about 3 KB of the 227 KB a CTA may use
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(apply_plane_kernel<T, P, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 223 * 1024);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(apply_plane_kernel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     224 * 1024);
+                                     223 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }

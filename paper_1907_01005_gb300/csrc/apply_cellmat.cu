@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
     float* U = reinterpret_cast<float*>(sm + G::OFF_U);    // gathered patch tensor, then the cells' results
     float* Vs = reinterpret_cast<float*>(sm + G::OFF_V);   // [8][N3]
     __shared__ int32_t sOff[kUnitBlocks][8], sHout[kUnitBlocks][8], sHin[kUnitBlocks][8];
+    __shared__ int sHn[kUnitBlocks][8], sHb[kUnitBlocks][8];   // fetched halo slots: elements, buffer offsets
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
     __shared__ int sNode[NPN];
     __shared__ int64_t sItem;
@@ -454,23 +455,21 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
             if (tid == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
             if (warp == 0 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) && tid == 0)
                 atomicExch(a.status, kDevTimeout);
-            __syncthreads();
-            for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
-                const int node = e >> 2, bb = e & 3;
-                if (bb >= nb) continue;
-                const int ne = sNode[node];
-                if (((ne >> 16) & 7) != 7) continue;
-                const int32_t o = sOff[bb][7];
-                if (o < 0) continue;
-                const int ldb = sLd[bb];
-                const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
-                put_own_row<P>(a.Y + (int64_t)o * 4 + (ne & 0xffff) * ldb, U + node * S + sBase[bb], ldb,
-                               (ne & kBoundary) != 0, (ne >> kAuxShift) & 7, a.halo, sHin[bb], i, j, k, px, py, pz);
+            // the halos addressed to this unit, fetched into the free A tiles
+            if (tid < kUnitBlocks * 8) {
+                const int bb = tid >> 3, e = tid & 7;
+                sHn[bb][e] = (e > 0 && bb < nb && sOff[bb][7] >= 0 && sHin[bb][e] >= 0)
+                                 ? halo_slot_rows<P>(e, px, py, pz) * sLd[bb] : 0;
             }
-            __syncthreads();                               // the halo rows addressed to this unit are read
-            if (warp == 7)                                 // one warp drops them from L2
-                for (int bb = 0; bb < nb; ++bb)
-                    if (sOff[bb][7] >= 0) discard_halo<P>(a.halo, sHin[bb], sLd[bb], px, py, pz, tid & 31, 32);
+            __syncthreads();
+            float* hbuf = reinterpret_cast<float*>(sm + G::OFF_AH);
+            fetch_halo(hbuf, a.halo, sHin, sHn, sHb, nb);
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncthreads();
+            // own rows: own part plus the halo rows, stored once
+            store_own_rows<P>(
+                [&](int bb) -> float* { return sOff[bb][7] >= 0 ? a.Y + (int64_t)sOff[bb][7] * 4 : nullptr; }, U, S,
+                sBase, sLd, hbuf, sHb, sHn, sNode, nb, px, py, pz);
         }  // unit_ok
         else if (tid == 0 && in_mesh) {
             mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     T* Yp = U + G::UEX;                            // same layout, accumulated cell results
     T* Vs = Yp + G::TEN;                           // [8][N3]  V at the Gauss points
     __shared__ int32_t sOff[kUnitBlocks][8], sHout[kUnitBlocks][8], sHin[kUnitBlocks][8];
+    __shared__ int sHn[kUnitBlocks][8], sHb[kUnitBlocks][8];   // fetched halo slots: elements, buffer offsets
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
     __shared__ int sNode[NPN];                     // node_entry: row, owner slot, first-writer and boundary bits
     __shared__ int64_t sItem;
@@ -253,27 +254,23 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     }
     __syncthreads();
     if (tid == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
-    // (2) the upper neighbours' halos addressed to this patch
+    // (2) the upper neighbours' halos addressed to this patch, fetched into
+    // the free gather buffer in one round of asynchronous copies
     if (tid < 32 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) && tid == 0)
         atomicExch(a.status, kDevTimeout);
+    if (tid < kUnitBlocks * 8) {
+        const int b = tid >> 3, e = tid & 7;
+        sHn[b][e] = (e > 0 && b < nb && sOff[b][7] >= 0 && sHin[b][e] >= 0)
+                        ? halo_slot_rows<P>(e, px, py, pz) * sLd[b] : 0;
+    }
+    __syncthreads();
+    fetch_halo(U, a.halo, sHin, sHn, sHb, nb);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     // (3) own rows: own part plus the halo rows, stored once
-    for (int e = tid; e < NPN * kUnitBlocks; e += blockDim.x) {
-        const int node = e >> 2, b = e & 3;
-        if (b >= nb) continue;
-        const int ne = sNode[node];
-        if (((ne >> 16) & 7) != 7) continue;
-        const int32_t o = sOff[b][7];
-        if (o < 0) continue;
-        const int ld = sLd[b];
-        const int i = node % NP, j = (node / NP) % NP, k = node / (NP * NP);
-        put_own_row<P>(a.Y + (int64_t)o * kElem16 + (ne & 0xffff) * ld, Yp + node * S + sBase[b], ld,
-                       (ne & kBoundary) != 0, (ne >> kAuxShift) & 7, a.halo, sHin[b], i, j, k, px, py, pz);
-    }
-    __syncthreads();                                   // the halo rows addressed to this unit are read
-    if (tid >= (int)blockDim.x - 32)                   // one warp drops them from L2
-        for (int b = 0; b < nb; ++b)
-            if (sOff[b][7] >= 0) discard_halo<P>(a.halo, sHin[b], sLd[b], px, py, pz, tid & 31, 32);
+    store_own_rows<P>(
+        [&](int b) -> T* { return sOff[b][7] >= 0 ? a.Y + (int64_t)sOff[b][7] * kElem16 : nullptr; }, Yp, S, sBase,
+        sLd, U, sHb, sHn, sNode, nb, px, py, pz);
     }  // unit_ok
     else if (tid == 0 && in_mesh) {
         mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it

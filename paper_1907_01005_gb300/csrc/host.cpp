@@ -751,10 +751,7 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                         const int64_t rows = (int64_t)(ex ? 1 : n3[0]) * (ey ? 1 : n3[1]) * (ez ? 1 : n3[2]);
                         if (h * (int64_t)b->elem() / 16 >= (int64_t)INT32_MAX) throw std::bad_alloc();
                         b->hslot[(size_t)k * 8 + e] = int32_t(h * (int64_t)b->elem() / 16);
-                        // slots start on 128-byte lines: the owner discards them
-                        // from L2 once read, without touching a neighbour's slot
-                        const int64_t per_line = 128 / (int64_t)b->elem();
-                        h += (rows * b->ld[b->col_idx[k]] + per_line - 1) / per_line * per_line;
+                        h += rows * b->ld[b->col_idx[k]];   // a multiple of 16 bytes
                     }
             }
             b->halo_elems = h;
@@ -1158,7 +1155,7 @@ int choose_cells_per_round(int p, int wmax, int ldmax, int dtype, int& cpr) {
         const size_t smem = dtype == FE_F64 ? apply_smem_bytes<double>(p, wmax, ldmax, c)
                                             : apply_smem_bytes<float>(p, wmax, ldmax, c);
         const int thr = apply_threads<float>(p, wmax, c);
-        if (smem <= 224 * 1024 && thr <= apply_max_threads(p)) {   // 3 KB of static node tables
+        if (smem <= 223 * 1024 && thr <= apply_max_threads(p)) {   // about 3 KB of static node and halo tables
             cpr = c;
             return FE_OK;
         }

@@ -12,8 +12,10 @@
 // work item (1) stores its contributions to its lower neighbours' rows in
 // halo slots of their own (block, e), then marks its patch; (2) waits,
 // bounded in time, until its (at most 7) upper neighbours have marked theirs;
-// (3) adds to its own rows the halo rows addressed to them, in a fixed order
-// (own part, then e = 1 .. 7), and stores every row of its own blocks once.
+// (3) fetches the halo rows addressed to its own blocks into shared memory
+// (one round of asynchronous copies), adds them to its own rows in a fixed
+// order (own part, then e = 1 .. 7), and stores every row of its own blocks
+// once.
 // No step waits on anything but halo writes, which never wait, so the waits
 // stay one level deep.  Y gets no zero-fill, no atomics and no
 // read-modify-write, and the same bits on every run.
@@ -138,47 +140,121 @@ __device__ __forceinline__ void put_halo_row(T* dst, const T* ys, int ld) {
         __stcg(reinterpret_cast<V*>(dst + c0), *reinterpret_cast<const V*>(ys + c0));
 }
 
-// An own row of Y: the patch's part (ys), plus the halo rows of the upper
-// neighbours e within the face mask f (halo + hin[e] 16-byte units + the
-// row's face index times ld), added in the order e = 1 .. 7; zeros for a
-// boundary node.  Stored once.
-template <int P, typename T>
-__device__ __forceinline__ void put_own_row(T* yd, const T* ys, int ld, bool zero, int f, const T* halo,
-                                            const int32_t* hin, int i, int j, int k, int px, int py, int pz) {
-    using V = typename V16<T>::type;
-    constexpr int kElem16 = 16 / sizeof(T);
-    const T* src[7];
-    int ns = 0;
-    if (!zero) {
+// Rows of the halo slot of upper-neighbour offset e for an own block of
+// patch (px, py, pz): the product over the directions with e_d = 0 of the
+// own node range 2p + [p_d == 0].
+template <int P>
+__device__ __forceinline__ int halo_slot_rows(int e, int px, int py, int pz) {
+    constexpr int Q = 2 * P;
+    return ((e & 1) ? 1 : Q + (px == 0)) * ((e & 2) ? 1 : Q + (py == 0)) * ((e & 4) ? 1 : Q + (pz == 0));
+}
+
+// Copies the halo slots addressed to a work item's own blocks into shared
+// memory with 16-byte asynchronous copies, so that the own rows are summed
+// from shared memory: slot (b, e) of nslot[b][e] elements (0 where there is
+// none; a whole number of 16-byte chunks) from halo + hin[b][e] 16-byte units
+// to hbuf + base[b][e], the slots packed in the order (b, e).  base is filled
+// here by warp 0 (a prefix sum over the at most 32 slots).  The chunks of all
+// slots are then dealt to the threads in one flat range: a thread first
+// works out the source and destination of each of its chunks (a binary search
+// over the slot starts) and only then issues its copies back to back.  The
+// caller waits (cp.async.wait_all) and synchronises before reading hbuf.
+template <typename T>
+__device__ __forceinline__ void fetch_halo(T* hbuf, const T* halo, const int32_t (*hin)[8], const int (*nslot)[8],
+                                           int (*base)[8], int nblocks) {
+    constexpr int CH = 16 / sizeof(T);
+    if (threadIdx.x < 32) {
+        const int b = threadIdx.x >> 3, e = threadIdx.x & 7;
+        const int n = b < nblocks ? nslot[b][e] : 0;
+        int v = n;
 #pragma unroll
-        for (int e = 1; e < 8; ++e)
-            if ((f & e) == e && hin[e] >= 0)
-                src[ns++] = halo + (int64_t)hin[e] * kElem16 + halo_face_index<P>(e, i, j, k, px, py, pz) * ld;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if ((int)(threadIdx.x & 31) >= o) v += y;
+        }
+        if (b < nblocks) base[b][e] = v - n;
     }
-    for (int c0 = 0; c0 < ld; c0 += V16<T>::n) {
-        V v = zero ? V16<T>::zero() : *reinterpret_cast<const V*>(ys + c0);
-        for (int q = 0; q < ns; ++q) V16<T>::add(v, __ldcg(reinterpret_cast<const V*>(src[q] + c0)));
-        __stcg(reinterpret_cast<V*>(yd + c0), v);
+    __syncthreads();
+    if (nblocks <= 0) return;
+    const int nq = 8 * nblocks;                       // slots q = 8 b + e
+    const int* bflat = &base[0][0];
+    const int total = (bflat[nq - 1] + nslot[nblocks - 1][7]) / CH;
+    const unsigned dst0 = (unsigned)__cvta_generic_to_shared(hbuf);
+    constexpr int K = 4;                              // chunks per thread resolved before issuing
+    for (int c0 = 0; c0 < total; c0 += K * (int)blockDim.x) {
+        const T* src[K];
+        unsigned dst[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int c = c0 + (int)threadIdx.x + k * (int)blockDim.x;
+            src[k] = nullptr;
+            dst[k] = 0u;
+            if (c < total) {
+                // the last slot q with base <= c * CH (empty slots share their
+                // start with the next one, so q is the slot holding chunk c)
+                int q = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (q + step < nq && bflat[q + step] <= c * CH) q += step;
+                const int r = c * CH - bflat[q];
+                src[k] = halo + (int64_t)hin[q >> 3][q & 7] * CH + r;
+                dst[k] = dst0 + (unsigned)((bflat[q] + r) * (int)sizeof(T));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (src[k] != nullptr)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst[k]), "l"(src[k]) : "memory");
     }
 }
 
-// Drops from L2, without a write-back, the halo slots of an own block once
-// all of them are read (no one reads them again before the next apply
-// rewrites them): slot e holds (2p + [px == 0]) ... rows over the directions
-// with e_d = 0, of ld elements; thread t of nt takes every nt-th 128-byte
-// line.  The slots start on 128-byte lines (host layout).
-template <int P, typename T>
-__device__ __forceinline__ void discard_halo(const T* halo, const int32_t* hin, int ld, int px, int py, int pz,
-                                             int t, int nt) {
-    constexpr int Q = 2 * P;
-#pragma unroll 1
-    for (int e = 1; e < 8; ++e) {
-        if (hin[e] < 0) continue;
-        const int rows = ((e & 1) ? 1 : Q + (px == 0)) * ((e & 2) ? 1 : Q + (py == 0)) * ((e & 4) ? 1 : Q + (pz == 0));
-        const int lines = (int)(((int64_t)rows * ld * (int)sizeof(T) + 127) / 128);
-        const char* base = reinterpret_cast<const char*>(halo) + (int64_t)hin[e] * 16;
-        for (int l = t; l < lines; l += nt)
-            asm volatile("discard.global.L2 [%0], 128;" ::"l"(base + 128 * (int64_t)l) : "memory");
+// Stores the own rows of every block into Y: the patch's part (the patch
+// tensor yp: node row stride S elements, block b at column colbase[b], ld[b]
+// columns) plus the fetched halo rows of the upper neighbours e within the
+// node's face mask (slot (b, e) at hbuf + hb[b][e] where nslot[b][e] > 0,
+// the row at its halo_face_index), added in the order e = 1 .. 7, so every
+// row has the same rounding on every run; zeros for boundary nodes.  Block
+// b's own rows form one contiguous range of Y starting at own_row0(b) (rows
+// x fastest over the own range), so the threads take its 16-byte chunks in
+// address order and a warp's stores cover consecutive addresses.  Blocks
+// with no own rows here have own_row0(b) == nullptr.
+template <int P, typename T, typename OwnRow0>
+__device__ __forceinline__ void store_own_rows(OwnRow0 own_row0, const T* yp, int S, const int* colbase,
+                                               const int* ld, const T* hbuf, const int (*hb)[8],
+                                               const int (*nslot)[8], const int* node_tab, int nblocks, int px,
+                                               int py, int pz) {
+    using V = typename V16<T>::type;
+    constexpr int CH = 16 / sizeof(T), Q = 2 * P, NP = 2 * P + 1;
+    const int lx = px > 0, ly = py > 0, lz = pz > 0;   // own range [l, 2p] per direction
+    const int nx = Q + 1 - lx, ny = Q + 1 - ly, nz = Q + 1 - lz;
+    const int rows = nx * ny * nz;
+    for (int b = 0; b < nblocks; ++b) {
+        T* yd = own_row0(b);
+        if (yd == nullptr) continue;
+        const int ldb = ld[b], cpr = ldb / CH, total = rows * cpr;
+        for (int c = threadIdx.x; c < total; c += blockDim.x) {
+            const int r = c / cpr, cc = c - r * cpr;
+            // the own range has 2p or 2p + 1 nodes: divisions by constants
+            const int rx = lx ? r % Q : r % (Q + 1), ryz = lx ? r / Q : r / (Q + 1);
+            const int ry = ly ? ryz % Q : ryz % (Q + 1), rz = ly ? ryz / Q : ryz / (Q + 1);
+            const int i = lx + rx, j = ly + ry, k = lz + rz;
+            const int node = i + NP * (j + NP * k);
+            const int ne = node_tab[node];
+            V v = V16<T>::zero();
+            if (!(ne & kBoundary)) {
+                v = *reinterpret_cast<const V*>(yp + node * S + colbase[b] + cc * CH);
+                const int f = (ne >> kAuxShift) & 7;
+                if (f) {
+#pragma unroll
+                    for (int e = 1; e < 8; ++e)
+                        if ((f & e) == e && nslot[b][e] > 0)
+                            V16<T>::add(v, *reinterpret_cast<const V*>(
+                                               hbuf + hb[b][e] + halo_face_index<P>(e, i, j, k, px, py, pz) * ldb +
+                                               cc * CH));
+                }
+            }
+            __stcg(reinterpret_cast<V*>(yd) + c, v);
+        }
     }
 }
 
