@@ -297,17 +297,20 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
         put_halo_row(a.halo + (int64_t)h * kElem16 + (ne >> kAuxShift) * ld, Yp + node * ld, ld);
     }
     __syncthreads();
-    if (threadIdx.x == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+    // the patch is marked by a thread outside warp 0 while warp 0 waits for
+    // the neighbours
+    if (threadIdx.x == (blockDim.x > 32 ? 32u : 0u)) mark_done(a.done, px + a.npx * (py + a.npy * pz));
     if (threadIdx.x < 32 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) &&
         threadIdx.x == 0)
         atomicExch(a.status, kDevTimeout);
     const int64_t oown = sOff[7];
     // the halos addressed to this tile, fetched into the free gather buffer
+    // (slot sizes by lanes 0..7 of warp 0, the lanes that read them in the
+    // prefix of fetch_halo; its barrier publishes them)
     if (threadIdx.x < 8) {
         const int e = threadIdx.x;
         sHn[0][e] = (e > 0 && oown >= 0 && sHin[0][e] >= 0) ? halo_slot_rows<P>(e, px, py, pz) * ld : 0;
     }
-    __syncthreads();
     fetch_halo(U, a.halo, sHin, sHn, sHb, 1);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();

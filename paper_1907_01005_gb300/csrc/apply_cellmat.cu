@@ -452,16 +452,18 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
                 put_halo_row(a.halo + (int64_t)h * 4 + (ne >> kAuxShift) * ldb, U + node * S + sBase[bb], ldb);
             }
             __syncthreads();
-            if (tid == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+            // the patch is marked by warp 1 while warp 0 waits for the neighbours
+            if (tid == 32) mark_done(a.done, px + a.npx * (py + a.npy * pz));
             if (warp == 0 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) && tid == 0)
                 atomicExch(a.status, kDevTimeout);
             // the halos addressed to this unit, fetched into the free A tiles
+            // (slot sizes by warp 0, whose lanes read them in the prefix of
+            // fetch_halo; its barrier publishes them)
             if (tid < kUnitBlocks * 8) {
                 const int bb = tid >> 3, e = tid & 7;
                 sHn[bb][e] = (e > 0 && bb < nb && sOff[bb][7] >= 0 && sHin[bb][e] >= 0)
                                  ? halo_slot_rows<P>(e, px, py, pz) * sLd[bb] : 0;
             }
-            __syncthreads();
             float* hbuf = reinterpret_cast<float*>(sm + G::OFF_AH);
             fetch_halo(hbuf, a.halo, sHin, sHn, sHb, nb);
             asm volatile("cp.async.wait_all;\n" ::: "memory");

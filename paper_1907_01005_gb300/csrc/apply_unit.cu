@@ -107,6 +107,10 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         sOff[tid >> 3][tid & 7] = has ? unit.off[tid >> 3][tid & 7] : -1;
         sHout[tid >> 3][tid & 7] = has ? unit.hout[tid >> 3][tid & 7] : -1;
         sHin[tid >> 3][tid & 7] = has ? unit.hin[tid >> 3][tid & 7] : -1;
+        // elements of the halo slots (b, e) this unit fetches for its own rows
+        const int hb = tid >> 3, he = tid & 7;
+        sHn[hb][he] = (he > 0 && has && unit.off[hb][7] >= 0 && unit.hin[hb][he] >= 0)
+                          ? halo_slot_rows<P>(he, px, py, pz) * unit.ld[hb] : 0;
     }
     if (tid == 0) {
         int base = 0;
@@ -253,17 +257,13 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         put_halo_row(a.halo + (int64_t)h * kElem16 + (ne >> kAuxShift) * ld, Yp + node * S + sBase[b], ld);
     }
     __syncthreads();
-    if (tid == 0) mark_done(a.done, px + a.npx * (py + a.npy * pz));
+    // the patch is marked by warp 1 while warp 0 waits for the neighbours
+    if (tid == 32) mark_done(a.done, px + a.npx * (py + a.npy * pz));
     // (2) the upper neighbours' halos addressed to this patch, fetched into
-    // the free gather buffer in one round of asynchronous copies
+    // the free gather buffer in one round of asynchronous copies (the
+    // barrier in fetch_halo holds the other warps until warp 0 is through)
     if (tid < 32 && !wait_upper_neighbours(a.done, a.count, px, py, pz, a.npx, a.npy, a.npz) && tid == 0)
         atomicExch(a.status, kDevTimeout);
-    if (tid < kUnitBlocks * 8) {
-        const int b = tid >> 3, e = tid & 7;
-        sHn[b][e] = (e > 0 && b < nb && sOff[b][7] >= 0 && sHin[b][e] >= 0)
-                        ? halo_slot_rows<P>(e, px, py, pz) * sLd[b] : 0;
-    }
-    __syncthreads();
     fetch_halo(U, a.halo, sHin, sHn, sHb, nb);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();

@@ -232,13 +232,15 @@ __device__ __forceinline__ void store_own_rows(OwnRow0 own_row0, const T* yp, in
         T* yd = own_row0(b);
         if (yd == nullptr) continue;
         const int ldb = ld[b], cpr = ldb / CH, total = rows * cpr;
+        int hbe[8];                                    // slot starts, -1 where there is no halo
+#pragma unroll
+        for (int e = 1; e < 8; ++e) hbe[e] = nslot[b][e] > 0 ? hb[b][e] : -1;
         for (int c = threadIdx.x; c < total; c += blockDim.x) {
             const int r = c / cpr, cc = c - r * cpr;
-            // the own range has 2p or 2p + 1 nodes: divisions by constants
+            // own-range coordinates (2p or 2p + 1 nodes: divisions by constants)
             const int rx = lx ? r % Q : r % (Q + 1), ryz = lx ? r / Q : r / (Q + 1);
             const int ry = ly ? ryz % Q : ryz % (Q + 1), rz = ly ? ryz / Q : ryz / (Q + 1);
-            const int i = lx + rx, j = ly + ry, k = lz + rz;
-            const int node = i + NP * (j + NP * k);
+            const int node = (lx + rx) + NP * ((ly + ry) + NP * (lz + rz));
             const int ne = node_tab[node];
             V v = V16<T>::zero();
             if (!(ne & kBoundary)) {
@@ -246,11 +248,16 @@ __device__ __forceinline__ void store_own_rows(OwnRow0 own_row0, const T* yp, in
                 const int f = (ne >> kAuxShift) & 7;
                 if (f) {
 #pragma unroll
-                    for (int e = 1; e < 8; ++e)
-                        if ((f & e) == e && nslot[b][e] > 0)
-                            V16<T>::add(v, *reinterpret_cast<const V*>(
-                                               hbuf + hb[b][e] + halo_face_index<P>(e, i, j, k, px, py, pz) * ldb +
-                                               cc * CH));
+                    for (int e = 1; e < 8; ++e) {
+                        if ((f & e) != e || hbe[e] < 0) continue;
+                        // halo_face_index in own-range coordinates: the free
+                        // directions (e_d = 0), x fastest
+                        int idx = 0, st = 1;
+                        if (!(e & 1)) { idx += rx * st; st *= nx; }
+                        if (!(e & 2)) { idx += ry * st; st *= ny; }
+                        if (!(e & 4)) idx += rz * st;
+                        V16<T>::add(v, *reinterpret_cast<const V*>(hbuf + hbe[e] + idx * ldb + cc * CH));
+                    }
                 }
             }
             __stcg(reinterpret_cast<V*>(yd) + c, v);
