@@ -125,6 +125,7 @@ struct GramTcArgs {
     const int32_t* col_info;    // (slot << 16) | (column in block << 8) | row stride of the block
     const int32_t* col_glob;    // global column id
     const int32_t* rows;        // rows of each row block
+    int16_t* item_exp;          // scratch: item exponents, 2 x gram_tc_tile() per item (A side, B side)
     int32_t n_cols;
     double* G;
     int32_t* status;            // device status word (set on a malformed work item)

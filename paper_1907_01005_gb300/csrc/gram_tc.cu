@@ -25,7 +25,8 @@
 // The epilogue turns the class sums of an output element into one integer in
 // units of 2^-(8 LMAX) of 2^(E_m + E_n), converts it to FP64 with integer
 // operations only (the FP64 pipe of this GPU is slow) and adds it into the
-// dense FP64 result with one atomic (and its mirror for symmetric products).
+// dense FP64 result with one atomic (symmetric products: into the upper
+// triangle, mirrored by a small kernel at the end).
 //
 // Tiles.  An item computes a 128 x N tile (mi, ni) of its group's union
 // columns: operand A of the MMA is the panel of the tile's 128 A columns
@@ -73,7 +74,7 @@ constexpr int kMmaWarp = kProdWarps + kEpiWarps;          // warp 24
 constexpr int kThreads = 32 * (kMmaWarp + 1);            // 800
 static_assert(kProdWarps % 4 == 0, "the epilogue warps must cover the four tensor-memory lane quadrants in order");
 constexpr int kProdThreads = 32 * kProdWarps, kEpiThreads = 32 * kEpiWarps;
-constexpr int kBarProd = 1, kBarEpi = 2, kBarQuad = 3;   // named barriers: warp groups, quad numbering
+constexpr int kBarProd = 1, kBarEpi = 2, kBarProd1 = 3;  // named barriers: producer groups 0 and 1, epilogue
 constexpr int kNone = -30000;             // exponent of an all-zero column
 constexpr int kMaxRows = (2 * kMaxP + 1) * (2 * kMaxP + 1) * (2 * kMaxP + 1);   // rows of a row block
 constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;   // bounded mbarrier waits (0.2 s)
@@ -133,19 +134,37 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
     }
 }
 
-// 32 lanes x 8 consecutive FP32 columns of tensor memory: thread i of the
-// warp receives lane (32 (warp % 4) + i), columns col .. col + 7.  The wait
-// is tied to the destination registers so that no use moves above it.
-__device__ __forceinline__ void tmem_load8(uint32_t taddr, float (&v)[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
-                 :: "memory");
+// Tensor-memory loads: thread i of a warp receives lane (32 (warp % 4) + i)
+// of the columns loaded.
+// The NCLS level classes of 8 consecutive columns: NCLS loads of 32 lanes x 8
+// columns (column col + k kST for class k), then one wait.  The wait (and an
+// empty statement for the second half of the registers) is tied to the
+// destination registers so that no use moves above it.
+template <int NCLS>
+__device__ __forceinline__ void tmem_load_classes(uint32_t taddr, float (&v)[NCLS][8]) {
+    static_assert(NCLS == 2 || NCLS == 4, "two or four level classes");
+    uint32_t r[NCLS][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+    for (int k = 0; k < NCLS; ++k)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[k][0]), "=r"(r[k][1]), "=r"(r[k][2]), "=r"(r[k][3]), "=r"(r[k][4]), "=r"(r[k][5]),
+                       "=r"(r[k][6]), "=r"(r[k][7])
+                     : "r"(taddr + (uint32_t)(k * kST)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[0][4]), "+r"(r[0][5]),
+                   "+r"(r[0][6]), "+r"(r[0][7]), "+r"(r[1][0]), "+r"(r[1][1]), "+r"(r[1][2]), "+r"(r[1][3]),
+                   "+r"(r[1][4]), "+r"(r[1][5]), "+r"(r[1][6]), "+r"(r[1][7])
+                 :: "memory");
+    if constexpr (NCLS == 4)
+        asm volatile(""
+                     : "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]), "+r"(r[2][4]), "+r"(r[2][5]),
+                       "+r"(r[2][6]), "+r"(r[2][7]), "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]),
+                       "+r"(r[3][4]), "+r"(r[3][5]), "+r"(r[3][6]), "+r"(r[3][7])
+                     :: "memory");
+#pragma unroll
+    for (int k = 0; k < NCLS; ++k)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[k][i] = __uint_as_float(r[k][i]);
 }
 
 // ---- numerics helpers ------------------------------------------------------------
@@ -186,57 +205,6 @@ __device__ __forceinline__ long long round_scaled_i64(float v) {
     const float hi = rintf(v * pow2f(H));
     const float rem = fmaf(-hi, pow2f(-H), v);               // exact
     return ((long long)(int)hi << (U - H)) + (long long)__float2int_rn(rem * pow2f(U));
-}
-
-// Loads rows kstart .. kstart+7 of the group (those at or past kend read as
-// zero) of one union column into v and returns max |x|.  Consecutive rows of
-// a row block are ld elements apart.  When the 8 rows touch at most two row
-// blocks (always for p >= 2, whose row blocks hold at least 64 rows) the
-// addresses come from two bases and all loads are independent; otherwise the
-// rows are walked one by one.
-__device__ __forceinline__ float load8(const float* __restrict__ X, int ci, const int64_t* sOff, int n_u,
-                                       const int* sPref, int nrb, int kstart, int kend, float (&v)[8]) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = 0.f;
-    if (ci < 0 || kstart >= kend) return 0.f;
-    const int slot = ci >> 16, a = (ci >> 8) & 0xff, ld = ci & 0xff;
-    int r = 0;
-    while (r < nrb - 1 && kstart >= sPref[r + 1]) ++r;
-    const int end_r = sPref[r + 1];
-    if (r + 1 >= nrb || sPref[r + 2] >= kstart + 8) {
-        const int64_t o0 = sOff[r * n_u + slot];
-        const int64_t o1 = r + 1 < nrb ? sOff[(r + 1) * n_u + slot] : -1;
-        const int64_t b0 = o0 + (int64_t)(kstart - sPref[r]) * ld + a;   // row kstart + i -> b0 + i ld
-        const int64_t b1 = o1 + a - (int64_t)end_r * ld;                  // row k >= end_r -> b1 + k ld
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = kstart + i;
-            const bool in0 = k < end_r;
-            const bool ok = k < kend && (in0 ? o0 >= 0 : o1 >= 0);
-            const int64_t ix = in0 ? b0 + (int64_t)i * ld : b1 + (int64_t)k * ld;
-            if (ok) v[i] = __ldg(X + ix);
-        }
-    } else {
-        int rr = r, e = end_r;
-        int64_t o = sOff[rr * n_u + slot];
-        int64_t idx = o + (int64_t)(kstart - sPref[rr]) * ld + a;
-        for (int i = 0; i < 8; ++i) {
-            const int k = kstart + i;
-            if (k >= kend) break;
-            if (k == e) {                     // first row of the next row block (k < kend <= sPref[nrb])
-                ++rr;
-                e = sPref[rr + 1];
-                o = sOff[rr * n_u + slot];
-                idx = o + a;
-            }
-            if (o >= 0) v[i] = __ldg(X + idx);
-            idx += ld;
-        }
-    }
-    float mx = 0.f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(v[i]));
-    return mx;
 }
 
 // Loads rows kstart .. kstart+7 of the group (those at or past kend read as
@@ -406,6 +374,111 @@ struct ItemMeta {
     int E[2][kST];
 };
 
+// Tables of one item for a group of 256 producer threads (8 warps): the
+// group's row-block offsets and row prefix, the tile's columns and their
+// 16-byte quads, and the normalisation factors of the columns.
+struct ItemTables {
+    int64_t off[kMaxGroup * kMaxUnion];   // element offset of block (row block, union slot) or -1
+    int pref[kMaxGroup + 1];              // row prefix of the group's row blocks
+    int col[2][kST];                      // col_info of tile column c (A side, B side), -1 beyond the tile
+    int quad[2][kST];                     // quads (quad_pack), numbered per side
+    int nq[2];
+    int wcnt[8];
+    float f1[2][kST], f2[2][kST];         // x 2^-E = (x f1) f2
+};
+constexpr int kGroupThreads = 256;
+
+// Builds the offsets, row prefix, tile columns and quads of an item: called
+// by the 256 threads of a group (gt = 0..255) with their named barrier.
+__device__ __forceinline__ void build_item_tables(ItemTables& T, const GramTcArgs& g, const GramTcItem& it,
+                                                  const GramTcGroup& gr, const ItemGeo& ig, int gt, int bar) {
+    const int gw = gt >> 5, lane = gt & 31;
+    for (int e = gt; e < ig.nrb * gr.n_u; e += kGroupThreads) T.off[e] = g.union_off[gr.u_base + e];
+    if (gw == 0) {                                    // row prefix of the group: a warp scan
+        int v = lane < ig.nrb ? g.rows[gr.r0 + lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 0) T.pref[0] = 0;
+        if (lane < ig.nrb) T.pref[lane + 1] = v;
+    }
+    // tile columns: A columns on threads 0..127, B columns on 128..255
+    const int side_t = gt >> 7, c_t = gt & (kST - 1);
+    const int wc_t = side_t ? ig.wb : ig.wa;
+    const int ci_t = c_t < wc_t ? g.col_info[gr.c_base + (side_t ? ig.ni : ig.mi) * kST + c_t] : -1;
+    T.col[side_t][c_t] = ci_t;
+    // quads: one per tile column that starts a 16-byte chunk of its block
+    // row (or starts the tile), numbered with warp ballots (warps 0-3: A
+    // side, 4-7: B side); the mask marks the chunk's columns that are tile
+    // columns of that block
+    const int a = (ci_t >> 8) & 0xff;
+    const bool head = ci_t >= 0 && ((a & 3) == 0 || c_t == 0);
+    const unsigned bal = __ballot_sync(0xffffffffu, head);
+    if (lane == 0) T.wcnt[gw] = __popc(bal);
+    group_sync(bar, kGroupThreads);
+    if (head) {
+        int pos = __popc(bal & ((1u << lane) - 1));
+        for (int w = 4 * side_t; w < gw; ++w) pos += T.wcnt[w];
+        const int u = ci_t >> 16, a0 = a & ~3, tc0 = c_t - (a & 3);
+        int mask = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int tc = tc0 + i;
+            if (tc >= 0 && tc < wc_t && (T.col[side_t][tc] >> 16) == u) mask |= 1 << i;
+        }
+        T.quad[side_t][pos] = quad_pack(u, a0, ci_t & 0xff, mask, tc0);
+    }
+    if (c_t == 0) T.nq[side_t] = T.wcnt[4 * side_t] + T.wcnt[4 * side_t + 1] + T.wcnt[4 * side_t + 2] + T.wcnt[4 * side_t + 3];
+    group_sync(bar, kGroupThreads);
+}
+
+// Item exponents, before the Gram kernel: for every tile column of an item
+// the bound 2^E of |x| over the item's rows (E = kNone for an all-zero
+// column), A side then B side (SAME: A only, B = A), as int16 at
+// item_exp[item][side][c].  One CTA of 256 threads per item; tasks are
+// (quad, 8-row group) with 16-byte loads.
+template <bool SYM, bool SAME, int ROWS>
+__global__ void __launch_bounds__(kGroupThreads) gram_exp_kernel(const GramTcArgs g) {
+    __shared__ ItemTables T;
+    __shared__ unsigned sMax[2][kST];
+    const int gt = threadIdx.x;
+    const int64_t item = blockIdx.x;
+    const GramTcItem it = g.items[item];
+    const GramTcGroup gr = g.groups[it.group];
+    const ItemGeo ig = item_geo<SYM, SAME, ROWS>(it, gr);
+    int16_t* out = g.item_exp + item * 2 * kST;
+    if (!ig.ok) {                                     // reported by the Gram kernel
+        out[gt] = (int16_t)kNone;
+        return;
+    }
+    sMax[gt >> 7][gt & (kST - 1)] = 0u;
+    build_item_tables(T, g, it, gr, ig, gt, 1);
+    const int ngr = (it.k1 - it.k0 + 7) >> 3;
+    for (int side = 0; side < (SAME ? 1 : 2); ++side) {
+        const float* X = side ? g.B : g.A;
+        const int nq = T.nq[side];
+        for (int t = gt; t < nq * ngr; t += kGroupThreads) {
+            const Quad qd = quad_unpack(T.quad[side][t % nq]);
+            float4 v[8];
+            load8q(X, qd.u, qd.a0, qd.ld, T.off, gr.n_u, T.pref, ig.nrb, it.k0 + 8 * (t / nq), it.k1, v);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!((qd.mask >> i) & 1)) continue;
+                float mx = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) mx = fmaxf(mx, fabsf(f4c(v[k], i)));
+                if (mx > 0.f) atomicMax(&sMax[side][qd.tc0 + i], __float_as_uint(mx));
+            }
+        }
+    }
+    __syncthreads();
+    const int side = gt >> 7, c = gt & (kST - 1);
+    const float mx = __uint_as_float(sMax[SAME ? 0 : side][c]);
+    out[gt] = (int16_t)(mx > 0.f ? ilogbf(mx) + 1 : kNone);
+}
+
 // SAME: P^T P on diagonal tiles, A = B (one panel); SA, SB slices; LMAX the
 // highest level kept; NCLS level classes; SYM upper tiles mirrored; NAT the
 // natural three-slice split; NST ring stages (2: a chunk in one 96 KB stage;
@@ -421,12 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                   "a chunk fits its stage");
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     unsigned char* ring = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
-    __shared__ int64_t sOff[kMaxGroup * kMaxUnion];
-    __shared__ int sCol[2][kST];
-    __shared__ int sQuad[2][kST], sNq[2], sWcnt[8];
-    __shared__ int sPref[kMaxGroup + 1];
-    __shared__ unsigned sMax[2][kST];
-    __shared__ float sF1[2][kST], sF2[2][kST];
+    __shared__ ItemTables sTab[2];                 // one per producer group
     __shared__ ItemMeta sMeta[2];
     __shared__ __align__(8) uint64_t bFull[2], bEmpty[2], bTFull[2], bTEmpty[2], bMFull[2], bMEmpty[2];
     __shared__ uint32_t sTmem;
@@ -458,8 +526,17 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
 
     if (warp < kProdWarps) {
         // ======================= producers =======================================
+        // Two groups of 8 warps.  Each builds its own copy of every item's
+        // tables; the chunks of the ring alternate between them (chunk n is
+        // group n % 2's, in stage n % 2), so that one group loads and slices
+        // while the other's chunk is in flight.  With a single stage (NST 1)
+        // group 0 takes every chunk.  Group 0 also hands the item metadata to
+        // the epilogue.
+        const int grp = warp >> 3, gt = tid & (kGroupThreads - 1);
+        const int bar = grp == 0 ? kBarProd : kBarProd1;
+        ItemTables& T = sTab[grp];
         int chunk_no = 0;
-        const int side_t = tid >> 7, c_t = tid & (kST - 1);    // this thread's tile column at table set-up
+        const int side_t = gt >> 7, c_t = gt & (kST - 1);   // this thread's tile column at table set-up
         for (int64_t item = blockIdx.x, il = 0; item < g.n_items; item += gridDim.x, ++il) {
             const GramTcItem it = g.items[item];
             const GramTcGroup gr = g.groups[it.group];
@@ -470,97 +547,38 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
             }
             const int slot = (int)(il & 1);
             const int nsides = SAME ? 1 : 2;
-            group_sync(kBarProd, kProdThreads);              // the previous item's tables are done with
-            for (int e = tid; e < ig.nrb * gr.n_u; e += kProdThreads) sOff[e] = g.union_off[gr.u_base + e];
-            if (warp == 0) {                                  // row prefix of the group: a warp scan
-                int v = lane < ig.nrb ? g.rows[gr.r0 + lane] : 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, v, o);
-                    if (lane >= o) v += y;
-                }
-                if (lane == 0) sPref[0] = 0;
-                if (lane < ig.nrb) sPref[lane + 1] = v;
-            }
-            // tile columns: A columns on threads 0..127, B columns on 128..255
-            const bool tab = tid < 2 * kST;
-            const int wc_t = side_t ? ig.wb : ig.wa;
-            const int ci_t = tab && c_t < wc_t ? g.col_info[gr.c_base + (side_t ? ig.ni : ig.mi) * kST + c_t] : -1;
-            if (tab) {
-                sCol[side_t][c_t] = ci_t;
-                sMax[side_t][c_t] = 0u;
-            }
-            group_sync(kBarProd, kProdThreads);
-            // quads: one per tile column that starts a 16-byte chunk of its
-            // block row (or starts the tile), numbered with warp ballots; the
-            // mask marks the chunk's columns that are tile columns of that block
-            if (warp < 8) {                                   // warps 0-3: A side, 4-7: B side
-                const int a = (ci_t >> 8) & 0xff;
-                const bool head = ci_t >= 0 && ((a & 3) == 0 || c_t == 0);
-                const unsigned bal = __ballot_sync(0xffffffffu, head);
-                if (lane == 0) sWcnt[warp] = __popc(bal);
-                asm volatile("bar.sync %0, %1;" ::"r"(kBarQuad), "r"(256) : "memory");
-                if (head) {
-                    int pos = __popc(bal & ((1u << lane) - 1));
-                    for (int w = 4 * side_t; w < warp; ++w) pos += sWcnt[w];
-                    const int u = ci_t >> 16, a0 = a & ~3, tc0 = c_t - (a & 3);
-                    int mask = 0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int tc = tc0 + i;
-                        if (tc >= 0 && tc < wc_t && (sCol[side_t][tc] >> 16) == u) mask |= 1 << i;
-                    }
-                    sQuad[side_t][pos] = quad_pack(u, a0, ci_t & 0xff, mask, tc0);
-                }
-                if (c_t == 0)
-                    sNq[side_t] = sWcnt[4 * side_t] + sWcnt[4 * side_t + 1] + sWcnt[4 * side_t + 2] + sWcnt[4 * side_t + 3];
-            }
-            group_sync(kBarProd, kProdThreads);
-            // ---- column bounds of the item's rows: tasks (quad, 8-row group) ------
-            const int ngr = (it.k1 - it.k0 + 7) >> 3;
-            for (int side = 0; side < nsides; ++side) {
-                const float* X = side ? g.B : g.A;
-                const int nq = sNq[side];
-                for (int t = tid; t < nq * ngr; t += kProdThreads) {
-                    const Quad qd = quad_unpack(sQuad[side][t % nq]);
-                    float4 v[8];
-                    load8q(X, qd.u, qd.a0, qd.ld, sOff, gr.n_u, sPref, ig.nrb, it.k0 + 8 * (t / nq), it.k1, v);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (!((qd.mask >> i) & 1)) continue;
-                        float mx = 0.f;
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) mx = fmaxf(mx, fabsf(f4c(v[k], i)));
-                        if (mx > 0.f) atomicMax(&sMax[side][qd.tc0 + i], __float_as_uint(mx));
-                    }
-                }
-            }
-            // ---- the metadata slot is free once the epilogue of item il - 2 is done
-            if (tid == 0 && !mbar_wait(smem_u32(&bMEmpty[slot]), ((il >> 1) & 1) ^ 1, kWaitLimitNs)) sFail = 1;
-            group_sync(kBarProd, kProdThreads);
-            if (sFail) break;
-            // ---- item exponents: |x| < 2^E; x 2^-E = (x f1) f2 without underflow --
-            if (tab) {
-                const int sd = SAME ? 0 : side_t;
-                const float mx = __uint_as_float(sMax[sd][c_t]);
-                const int E = mx > 0.f ? ilogbf(mx) + 1 : kNone;
+            group_sync(bar, kGroupThreads);                  // the previous item's tables are done with
+            build_item_tables(T, g, it, gr, ig, gt, bar);
+            // ---- normalisation from the item exponents (|x| < 2^E) ----------------
+            const int sd = SAME ? 0 : side_t;
+            const int E = g.item_exp[item * 2 * kST + sd * kST + c_t];
+            {
                 const int e = E == kNone ? 0 : E;
-                if (side_t == sd) {
-                    sF1[side_t][c_t] = pow2f(-(e >> 1));
-                    sF2[side_t][c_t] = pow2f(-(e - (e >> 1)));
-                }
+                T.f1[side_t][c_t] = pow2f(-(e >> 1));
+                T.f2[side_t][c_t] = pow2f(-(e - (e >> 1)));
+            }
+            if (grp == 0) {
+                // the metadata slot is free once the epilogue of item il - 2 is done
+                if (gt == 0 && !mbar_wait(smem_u32(&bMEmpty[slot]), ((il >> 1) & 1) ^ 1, kWaitLimitNs)) sFail = 1;
+                group_sync(bar, kGroupThreads);
+                if (sFail) break;
+                const int wc_t = side_t ? ig.wb : ig.wa;
                 const int col = (side_t ? ig.ni : ig.mi) * kST + c_t;
                 sMeta[slot].E[side_t][c_t] = E;
                 sMeta[slot].gcol[side_t][c_t] = c_t < wc_t ? g.col_glob[gr.c_base + col] : -1;
+                group_sync(bar, kGroupThreads);
+                if (gt == 0) mbar_arrive(smem_u32(&bMFull[slot]));
+            } else {
+                group_sync(bar, kGroupThreads);
+                if (sFail) break;
             }
-            group_sync(kBarProd, kProdThreads);
-            if (tid == 0) mbar_arrive(smem_u32(&bMFull[slot]));
             // ---- chunks of 64 rows: load, normalise, slice into a ring stage -------
             for (int j = 0; j < ig.nchunks; ++j, ++chunk_no) {
-                const int stage = NST == 2 ? (chunk_no & 1) : 0;
+                if ((NST == 2 ? (chunk_no & 1) : 0) != grp) continue;
+                const int stage = NST == 2 ? grp : 0;
                 const int use = NST == 2 ? (chunk_no >> 1) : chunk_no;
-                if (tid == 0 && !mbar_wait(smem_u32(&bEmpty[stage]), (use & 1) ^ 1, kWaitLimitNs)) sFail = 1;
-                group_sync(kBarProd, kProdThreads);
+                if (gt == 0 && !mbar_wait(smem_u32(&bEmpty[stage]), (use & 1) ^ 1, kWaitLimitNs)) sFail = 1;
+                group_sync(bar, kGroupThreads);
                 if (sFail) break;
                 unsigned char* bufA = ring + stage * kStage;
                 unsigned char* bufB = SAME ? bufA : bufA + bytesA;
@@ -568,22 +586,22 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                 for (int side = 0; side < nsides; ++side) {
                     const float* X = side ? g.B : g.A;
                     unsigned char* base = side ? bufB : bufA;
-                    const int nq = sNq[side];
+                    const int nq = T.nq[side];
                     // operand rows beyond the tile's columns are never read back:
                     // they are left as they are.  Neighbouring threads take the
                     // eight 8-row groups of a quad, so that the 16-byte slice
                     // stores of a warp land in all eight chunk positions of the
                     // swizzled rows (no bank conflicts).
-                    for (int t = tid; t < nq * 8; t += kProdThreads) {
-                        const Quad qd = quad_unpack(sQuad[side][t >> 3]);
+                    for (int t = gt; t < nq * 8; t += kGroupThreads) {
+                        const Quad qd = quad_unpack(T.quad[side][t >> 3]);
                         const int jj = t & 7;
                         float4 v[8];
-                        load8q(X, qd.u, qd.a0, qd.ld, sOff, gr.n_u, sPref, ig.nrb, c0 + 8 * jj, c1, v);
+                        load8q(X, qd.u, qd.a0, qd.ld, T.off, gr.n_u, T.pref, ig.nrb, c0 + 8 * jj, c1, v);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             if (!((qd.mask >> i) & 1)) continue;
                             const int tc = qd.tc0 + i;
-                            const float f1 = sF1[side][tc], f2 = sF2[side][tc];
+                            const float f1 = T.f1[side][tc], f2 = T.f2[side][tc];
                             float x[8];
 #pragma unroll
                             for (int k = 0; k < 8; ++k) x[k] = f4c(v[k], i) * f1;
@@ -593,8 +611,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                     }
                 }
                 fence_async_smem();
-                group_sync(kBarProd, kProdThreads);
-                if (tid == 0) mbar_arrive(smem_u32(&bFull[stage]));
+                group_sync(bar, kGroupThreads);
+                if (gt == 0) mbar_arrive(smem_u32(&bFull[stage]));
             }
             if (sFail) break;
         }
@@ -629,8 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                 // beyond N, or wholly below the diagonal of a diagonal tile
                 if (32 * quad >= ig.wa || n0 >= ig.N || (ig.diag && n0 + 7 < 32 * quad)) continue;
                 float cv[NCLS][8];
-#pragma unroll
-                for (int k = 0; k < NCLS; ++k) tmem_load8(tbase + (uint32_t)(k * kST + n0), cv[k]);
+                tmem_load_classes<NCLS>(tbase + (uint32_t)n0, cv);
                 if (gm < 0 || Ea == kNone) continue;
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -638,12 +655,19 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                     const int gn = mt.gcol[1][n], Eb = mt.E[1][n];
                     if (gn < 0 || Eb == kNone || (ig.diag && m > n)) continue;
                     float cc[NCLS];
+                    bool nz = false;
 #pragma unroll
-                    for (int k = 0; k < NCLS; ++k) cc[k] = cv[k][i];
+                    for (int k = 0; k < NCLS; ++k) {
+                        cc[k] = cv[k][i];
+                        nz = nz || cc[k] != 0.f;
+                    }
+                    if (!nz) continue;                        // columns that share no row of the item
                     const double val = i64_scaled_to_double(window_value<NCLS, U>(cc), Ea + Eb - U);
                     if (val == 0.0) continue;
+                    // symmetric products: the upper triangle only (gm <= gn
+                    // here, union columns being in ascending global order);
+                    // mirror_upper fills the lower one afterwards
                     atomicAdd(&g.G[(int64_t)gm * g.n_cols + gn], val);
-                    if (SYM && gm != gn) atomicAdd(&g.G[(int64_t)gn * g.n_cols + gm], val);
                 }
             }
             tc_fence_before();
@@ -727,6 +751,25 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
     }
 }
 
+// G[n][m] = G[m][n] for m < n: the lower triangle of a symmetric product
+// from the upper one that the Gram kernel accumulated.
+__global__ void __launch_bounds__(256) mirror_upper_kernel(double* __restrict__ G, int n) {
+    const int64_t total = (int64_t)n * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / n), c = (int)(idx - (int64_t)r * n);
+        if (r > c) G[idx] = G[(int64_t)c * n + r];
+    }
+}
+
+cudaError_t mirror_upper(double* G, int n, cudaStream_t s) {
+    const int64_t total = (int64_t)n * n;
+    if (total == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+    mirror_upper_kernel<<<grid, 256, 0, s>>>(G, n);
+    return cudaGetLastError();
+}
+
 template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS>
 cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
     constexpr int smem = 2 * kStage + 1024;
@@ -741,6 +784,10 @@ cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // the item exponents first (one CTA per item), then the persistent kernel
+    gram_exp_kernel<SYM, SAME, ROWS><<<(unsigned)g.n_items, kGroupThreads, 0, s>>>(g);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<int64_t>(g.n_items, (int64_t)sms);
     gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS><<<grid, kThreads, smem, s>>>(g);
@@ -761,12 +808,18 @@ cudaError_t launch_gram_tc(const GramTcArgs& g, GramMode mode, cudaStream_t s) {
             GramTcArgs d = g, o = g;
             d.n_items = g.n_items_diag;
             o.items = g.items + g.n_items_diag;
+            o.item_exp = g.item_exp + g.n_items_diag * 2 * kST;
             o.n_items = g.n_items - g.n_items_diag;
             cudaError_t e = launch_tc<5, 5, 6, 4, true, true, false, 2, kItemRowsPP>(d, s);
-            if (e != cudaSuccess) return e;
-            return launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP>(o, s);
+            if (e == cudaSuccess) e = launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP>(o, s);
+            if (e == cudaSuccess) e = mirror_upper(g.G, g.n_cols, s);
+            return e;
         }
-        case GramMode::PtYSym: return launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY>(g, s);
+        case GramMode::PtYSym: {
+            cudaError_t e = launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY>(g, s);
+            if (e == cudaSuccess) e = mirror_upper(g.G, g.n_cols, s);
+            return e;
+        }
         default: return launch_tc<3, 3, 4, 2, false, false, true, 2, kItemRowsPY>(g, s);
     }
 }

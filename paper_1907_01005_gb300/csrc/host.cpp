@@ -201,6 +201,7 @@ struct fe_bcsr {
     size_t off_ucol0 = 0, off_rbunion = 0, off_xround = 0;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
     size_t off_tcg = 0, off_tcpy = 0, off_tcps = 0, off_tcpp = 0, off_tcu = 0, off_tcci = 0, off_tccg = 0, off_tcrows = 0;
+    size_t off_tcexp_pp = 0, off_tcexp_py = 0;   // item exponents of P^T P and of P^T Y (both forms)
     size_t off_units = 0, off_ld = 0, off_ticket = 0, sync_bytes = 0, off_ucnt = 0, off_tcnt = 0;
     // work items of the apply per patch (by patch id px + npx (py + npy pz)):
     // packed units (p <= 2 and the cell-matrix form) and tiles (p >= 3)
@@ -1021,6 +1022,11 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_tcci = off;  off = align_up(off + b->tc_cinfo.size() * sizeof(int32_t), 256);
         b->off_tccg = off;  off = align_up(off + b->tc_cglob.size() * sizeof(int32_t), 256);
         b->off_tcrows = off; off = align_up(off + b->tc_rows.size() * sizeof(int32_t), 256);
+        // item exponents (2 x gram_tc_tile() int16 per item): P^T P apart from
+        // P^T Y, which may run at the same time on another stream
+        const size_t exp_item = 2 * (size_t)gram_tc_tile() * sizeof(int16_t);
+        b->off_tcexp_pp = off; off = align_up(off + b->tc_pp.size() * exp_item, 256);
+        b->off_tcexp_py = off; off = align_up(off + std::max(b->tc_py.size(), b->tc_ps.size()) * exp_item, 256);
         b->off_units = off; off = align_up(off + b->units.size() * sizeof(Unit), 256);
         // work counter of the apply (16 bytes) and the per-patch counters of
         // finished work items: zeroed together before every apply
@@ -1266,6 +1272,7 @@ int gram_tc_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaSt
     g.col_info = reinterpret_cast<const int32_t*>(t + A->off_tcci);
     g.col_glob = reinterpret_cast<const int32_t*>(t + A->off_tccg);
     g.rows = reinterpret_cast<const int32_t*>(t + A->off_tcrows);
+    g.item_exp = reinterpret_cast<int16_t*>(const_cast<char*>(t) + (pp ? A->off_tcexp_pp : A->off_tcexp_py));
     g.n_cols = A->n_cols;
     g.G = G;
     g.status = A->mesh ? A->mesh->status : nullptr;
