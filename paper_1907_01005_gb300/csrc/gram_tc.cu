@@ -69,11 +69,12 @@ constexpr int kItemRowsPP = 192;          // P^T P (level 4: (2^15 + 2^14 + 2^15
 constexpr int kItemRowsPY = 256;          // P^T Y (level 2: 2^16 256 = 2^24)
 constexpr int kPanel = kST * 128;         // bytes of one slice panel (128 operand rows of 128 bytes)
 constexpr int kStage = 96 * 1024;         // bytes of one ring stage (both operands of a chunk)
-constexpr int kProdWarps = 16, kEpiWarps = 8;
-constexpr int kMmaWarp = kProdWarps + kEpiWarps;          // warp 24
+// Warp roles: PW producer warps (groups of 8), 24 - PW epilogue warps, the MMA
+// warp last (warp 24).  P^T Y, whose staging is the heavier side, takes 16
+// producer warps; P^T P, whose epilogue (four classes) is, takes 16 epilogue
+// warps.
+constexpr int kMmaWarp = 24;
 constexpr int kThreads = 32 * (kMmaWarp + 1);            // 800
-static_assert(kProdWarps % 4 == 0, "the epilogue warps must cover the four tensor-memory lane quadrants in order");
-constexpr int kProdThreads = 32 * kProdWarps, kEpiThreads = 32 * kEpiWarps;
 constexpr int kBarProd = 1, kBarEpi = 2, kBarProd1 = 3;  // named barriers: producer groups 0 and 1, epilogue
 constexpr int kNone = -30000;             // exponent of an all-zero column
 constexpr int kMaxRows = (2 * kMaxP + 1) * (2 * kMaxP + 1) * (2 * kMaxP + 1);   // rows of a row block
@@ -483,9 +484,13 @@ __global__ void __launch_bounds__(kGroupThreads) gram_exp_kernel(const GramTcArg
 // highest level kept; NCLS level classes; SYM upper tiles mirrored; NAT the
 // natural three-slice split; NST ring stages (2: a chunk in one 96 KB stage;
 // 1: the two operands of a P^T P off-diagonal chunk across the whole 192 KB)
-template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS>
+template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS, int PW>
 __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g) {
     static_assert(!NAT || (SA == 3 && SB == 3), "natural slices: three per operand");
+    static_assert(PW == 8 || PW == 16, "one or two producer groups");
+    constexpr int EW = kMmaWarp - PW;                          // epilogue warps: 8 or 16
+    constexpr int kProdThreads = 32 * PW, kEpiThreads = 32 * EW;
+    constexpr int kEpiCols = kST / (EW / 4);                   // tile columns of an epilogue warp
     static_assert(NCLS * kST <= 512, "tensor memory: 128 columns per level class");
     constexpr int NSETS = 512 / (NCLS * kST);   // accumulator sets in tensor memory
     constexpr int U = 8 * LMAX;                 // the epilogue works in units of 2^-U
@@ -524,34 +529,46 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
     tc_fence_after();
     const uint32_t tmem = sTmem;
 
-    if (warp < kProdWarps) {
+    if (warp < PW) {
         // ======================= producers =======================================
-        // Two groups of 8 warps.  Each builds its own copy of every item's
-        // tables; the chunks of the ring alternate between them (chunk n is
-        // group n % 2's, in stage n % 2), so that one group loads and slices
-        // while the other's chunk is in flight.  With a single stage (NST 1)
-        // group 0 takes every chunk.  Group 0 also hands the item metadata to
-        // the epilogue.
+        // Groups of 8 warps (two, or one).  Each builds its own copy of every
+        // item's tables; with two groups the chunks of the ring alternate
+        // between them (chunk n is group n % 2's, in stage n % 2), so that one
+        // group loads and slices while the other's chunk is in flight.  With a
+        // single group or a single stage (NST 1) group 0 takes every chunk.
+        // Group 0 also hands the item metadata to the epilogue.
         const int grp = warp >> 3, gt = tid & (kGroupThreads - 1);
         const int bar = grp == 0 ? kBarProd : kBarProd1;
         ItemTables& T = sTab[grp];
         int chunk_no = 0;
         const int side_t = gt >> 7, c_t = gt & (kST - 1);   // this thread's tile column at table set-up
+        // the next item's records are fetched while the current one is worked
+        // on (the item, then, once it has arrived, its group)
+        GramTcItem it_next{};
+        GramTcGroup gr_next{};
+        bool have_next = false;
         for (int64_t item = blockIdx.x, il = 0; item < g.n_items; item += gridDim.x, ++il) {
-            const GramTcItem it = g.items[item];
-            const GramTcGroup gr = g.groups[it.group];
+            const GramTcItem it = have_next ? it_next : g.items[item];
+            const GramTcGroup gr = have_next ? gr_next : g.groups[it.group];
+            have_next = item + gridDim.x < g.n_items;
+            if (have_next) it_next = g.items[item + gridDim.x];
             const ItemGeo ig = item_geo<SYM, SAME, ROWS>(it, gr);
             if (!ig.ok) {
                 if (tid == 0 && g.status) atomicExch(g.status, kDevBadTile);
+                if (have_next) gr_next = g.groups[it_next.group];
                 continue;
             }
             const int slot = (int)(il & 1);
             const int nsides = SAME ? 1 : 2;
-            group_sync(bar, kGroupThreads);                  // the previous item's tables are done with
-            build_item_tables(T, g, it, gr, ig, gt, bar);
-            // ---- normalisation from the item exponents (|x| < 2^E) ----------------
+            // this thread's column: item exponent and global id, loaded with the tables
             const int sd = SAME ? 0 : side_t;
             const int E = g.item_exp[item * 2 * kST + sd * kST + c_t];
+            const int wc_t = side_t ? ig.wb : ig.wa;
+            const int gcol_t = grp == 0 && c_t < wc_t ? g.col_glob[gr.c_base + (side_t ? ig.ni : ig.mi) * kST + c_t] : -1;
+            group_sync(bar, kGroupThreads);                  // the previous item's tables are done with
+            build_item_tables(T, g, it, gr, ig, gt, bar);
+            if (have_next) gr_next = g.groups[it_next.group];
+            // ---- normalisation from the item exponents (|x| < 2^E) ----------------
             {
                 const int e = E == kNone ? 0 : E;
                 T.f1[side_t][c_t] = pow2f(-(e >> 1));
@@ -562,10 +579,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                 if (gt == 0 && !mbar_wait(smem_u32(&bMEmpty[slot]), ((il >> 1) & 1) ^ 1, kWaitLimitNs)) sFail = 1;
                 group_sync(bar, kGroupThreads);
                 if (sFail) break;
-                const int wc_t = side_t ? ig.wb : ig.wa;
-                const int col = (side_t ? ig.ni : ig.mi) * kST + c_t;
                 sMeta[slot].E[side_t][c_t] = E;
-                sMeta[slot].gcol[side_t][c_t] = c_t < wc_t ? g.col_glob[gr.c_base + col] : -1;
+                sMeta[slot].gcol[side_t][c_t] = gcol_t;
                 group_sync(bar, kGroupThreads);
                 if (gt == 0) mbar_arrive(smem_u32(&bMFull[slot]));
             } else {
@@ -574,8 +589,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
             }
             // ---- chunks of 64 rows: load, normalise, slice into a ring stage -------
             for (int j = 0; j < ig.nchunks; ++j, ++chunk_no) {
-                if ((NST == 2 ? (chunk_no & 1) : 0) != grp) continue;
-                const int stage = NST == 2 ? grp : 0;
+                constexpr bool kAlt = NST == 2 && PW == 16;   // chunks alternate between the groups
+                if ((kAlt ? (chunk_no & 1) : 0) != grp) continue;
+                const int stage = NST == 2 ? (chunk_no & 1) : 0;
                 const int use = NST == 2 ? (chunk_no >> 1) : chunk_no;
                 if (gt == 0 && !mbar_wait(smem_u32(&bEmpty[stage]), (use & 1) ^ 1, kWaitLimitNs)) sFail = 1;
                 group_sync(bar, kGroupThreads);
@@ -618,10 +634,10 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
         }
     } else if (warp < kMmaWarp) {
         // ======================= epilogue ========================================
-        const int ew = warp - kProdWarps;                 // 0..7
+        const int ew = warp - PW;                         // 0 .. EW - 1
         const int quad = ew & 3;                          // tensor-memory lanes 32 quad .. + 31
         const int m = 32 * quad + lane;                   // tile row (A column) of this thread
-        const int nhalf = ew >> 2;                        // tile columns [64 nhalf, 64 nhalf + 64)
+        const int part = ew >> 2;                         // tile columns [kEpiCols part, + kEpiCols)
         const int etid = tid - kProdThreads;
         for (int64_t item = blockIdx.x, il = 0; item < g.n_items; item += gridDim.x, ++il) {
             const GramTcItem it = g.items[item];
@@ -641,8 +657,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
             const int gm = mt.gcol[0][m], Ea = mt.E[0][m];
             const uint32_t tbase = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(set * NCLS * kST);
 #pragma unroll 1
-            for (int h = 0; h < kST / 16; ++h) {
-                const int n0 = 64 * nhalf + 8 * h;
+            for (int h = 0; h < kEpiCols / 8; ++h) {
+                const int n0 = kEpiCols * part + 8 * h;
                 // warp-uniform skips: lanes beyond the tile's A columns, columns
                 // beyond N, or wholly below the diagonal of a diagonal tile
                 if (32 * quad >= ig.wa || n0 >= ig.N || (ig.diag && n0 + 7 < 32 * quad)) continue;
@@ -770,12 +786,12 @@ cudaError_t mirror_upper(double* G, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS>
+template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS, int PW>
 cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
     constexpr int smem = 2 * kStage + 1024;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS>,
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
@@ -790,7 +806,7 @@ cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<int64_t>(g.n_items, (int64_t)sms);
-    gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS><<<grid, kThreads, smem, s>>>(g);
+    gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW><<<grid, kThreads, smem, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -810,17 +826,17 @@ cudaError_t launch_gram_tc(const GramTcArgs& g, GramMode mode, cudaStream_t s) {
             o.items = g.items + g.n_items_diag;
             o.item_exp = g.item_exp + g.n_items_diag * 2 * kST;
             o.n_items = g.n_items - g.n_items_diag;
-            cudaError_t e = launch_tc<5, 5, 6, 4, true, true, false, 2, kItemRowsPP>(d, s);
-            if (e == cudaSuccess) e = launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP>(o, s);
+            cudaError_t e = launch_tc<5, 5, 6, 4, true, true, false, 2, kItemRowsPP, 8>(d, s);
+            if (e == cudaSuccess) e = launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP, 8>(o, s);
             if (e == cudaSuccess) e = mirror_upper(g.G, g.n_cols, s);
             return e;
         }
         case GramMode::PtYSym: {
-            cudaError_t e = launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY>(g, s);
+            cudaError_t e = launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY, 16>(g, s);
             if (e == cudaSuccess) e = mirror_upper(g.G, g.n_cols, s);
             return e;
         }
-        default: return launch_tc<3, 3, 4, 2, false, false, true, 2, kItemRowsPY>(g, s);
+        default: return launch_tc<3, 3, 4, 2, false, false, true, 2, kItemRowsPY, 16>(g, s);
     }
 }
 
