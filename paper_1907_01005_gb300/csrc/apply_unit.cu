@@ -60,18 +60,37 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     __shared__ int sHn[kUnitBlocks][8], sHb[kUnitBlocks][8];   // fetched halo slots: elements, buffer offsets
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
     __shared__ int sNode[NPN];                     // node_entry: row, owner slot, first-writer and boundary bits
-    __shared__ int64_t sItem;
+    __shared__ __align__(16) Unit sUnit[2];        // the unit's record and the next one's
+    __shared__ int64_t sItem, sNext;
     const int tid = threadIdx.x;
     constexpr int kElem16 = 16 / sizeof(T);        // elements per 16-byte offset unit
+    // a unit record into sUnit[buf]: 16-byte asynchronous copies
+    static_assert(sizeof(Unit) % 16 == 0, "unit records are whole 16-byte chunks");
+    auto fetch_unit = [&](int64_t ticket_, int buf) {
+        if (tid < (int)(sizeof(Unit) / 16)) {
+            const char* src = reinterpret_cast<const char*>(a.units + (a.n_units - 1 - ticket_)) + 16 * tid;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&sUnit[buf]) + 16u * tid;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+        }
+    };
     // Units are taken from a work counter in descending order (descending
     // patch rank, the order of the write): one per CTA, or (persistent
-    // launch) until the list is exhausted.
+    // launch) until the list is exhausted.  A persistent CTA takes its next
+    // ticket as a unit starts and copies the next record in after the cell
+    // work, so neither round trip delays the next unit.
     if (tid == 0) sItem = (int64_t)atomicAdd(a.ticket, 1ull);
     __syncthreads();
     int64_t ticket = sItem;
+    int cur = 0;
+    if (ticket < a.n_units) fetch_unit(ticket, 0);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    unsigned long long next_raw = 0ull;            // thread 0: the next ticket
     while (ticket < a.n_units) {
     const int64_t item = a.n_units - 1 - ticket;
-    const Unit& unit = a.units[item];
+    const Unit& unit = sUnit[cur];
+    if (a.persistent && tid == 0) next_raw = atomicAdd(a.ticket, 1ull);
+    bool prefetched = false;
     const int px = unit.pxyz & 1023, py = (unit.pxyz >> 10) & 1023, pz = unit.pxyz >> 20;
     // Work-list check: the host packs 1..kUnitBlocks blocks with 1 <= width <= ld,
     // ld a whole number of 16-byte chunks, at most L lanes and sum(ld) <= kUnitLdSum.
@@ -241,7 +260,12 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
         // a fixed order, each node stored once
         merge_cells_store<P, S, NP, false>(t, cell, lane, b >= 0, U, Yp, base);
     }
+    if (a.persistent && tid == 0) sNext = (int64_t)next_raw;
     __syncthreads();
+    if (a.persistent) {                                // the next record, while this unit writes
+        if (sNext < a.n_units) fetch_unit(sNext, cur ^ 1);
+        prefetched = true;
+    }
 
     // ---- write into Y (Alg. 6, write step; unit_common.cuh) ------------------
     // (1) contributions to the lower neighbours' rows into their halo slots
@@ -275,11 +299,16 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     else if (tid == 0 && in_mesh) {
         mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it
     }
+    if (a.persistent && !prefetched) {                 // a skipped unit: the next record now
+        if (tid == 0) sNext = (int64_t)next_raw;
+        __syncthreads();
+        if (sNext < a.n_units) fetch_unit(sNext, cur ^ 1);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();                                   // the unit's rows are written (shared tables free)
-    if (tid == 0 && a.persistent) sItem = (int64_t)atomicAdd(a.ticket, 1ull);
     if (!a.persistent) break;
-    __syncthreads();
-    ticket = sItem;
+    ticket = sNext;
+    cur ^= 1;
     }
 }
 
