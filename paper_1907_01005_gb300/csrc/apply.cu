@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(max_threads<P>()) apply_plane_kernel(const App
     __syncthreads();
     // own rows: own part plus the halo rows, stored once
     store_own_rows<P>([&](int) -> T* { return oown >= 0 ? a.Y + oown : nullptr; }, Yp, ld, sCol0, sLd1, U, sHb, sHn,
-                      sNode, 1, px, py, pz);
+                      sNode, nullptr, 1, px, py, pz);
 }
 
 template <typename T, int P>

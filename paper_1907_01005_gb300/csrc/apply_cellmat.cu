@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(CmGeo<P>::THREADS, 2) apply_cellmat_kernel(con
             // own rows: own part plus the halo rows, stored once
             store_own_rows<P>(
                 [&](int bb) -> float* { return sOff[bb][7] >= 0 ? a.Y + (int64_t)sOff[bb][7] * 4 : nullptr; }, U, S,
-                sBase, sLd, hbuf, sHb, sHn, sNode, nb, px, py, pz);
+                sBase, sLd, hbuf, sHb, sHn, sNode, nullptr, nb, px, py, pz);
         }  // unit_ok
         else if (tid == 0 && in_mesh) {
             mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it

@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     __shared__ int sHn[kUnitBlocks][8], sHb[kUnitBlocks][8];   // fetched halo slots: elements, buffer offsets
     __shared__ int sLaneB[L], sLaneA[L], sMask[kUnitBlocks], sBase[kUnitBlocks], sLd[kUnitBlocks];
     __shared__ int sNode[NPN];                     // node_entry: row, owner slot, first-writer and boundary bits
+    __shared__ int sOwn[NPN];                      // own_row_entry of the patch's own rows
     __shared__ __align__(16) Unit sUnit[2];        // the unit's record and the next one's
     __shared__ int64_t sItem, sNext;
     const int tid = threadIdx.x;
@@ -143,6 +144,9 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     }
     for (int n = tid; n < NPN; n += blockDim.x)
         sNode[n] = node_entry<P>(n, px, py, pz, a.lx, a.ly, a.lz, a.dirichlet, a.npx, a.npy, a.npz);
+    // own-row table for the store, by the threads past the node table
+    for (int r = tid - NPN; r >= 0 && r < own_rows_of<P>(px, py, pz); r += blockDim.x - NPN)
+        sOwn[r] = own_row_entry<P>(r, px, py, pz);
     __syncthreads();
 
     static_assert(kUnitBlocks == 4, "task index: node << 2 | block");
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(UnitGeo<T, P>::THREADS, kUnitMinBlocks<T>)
     // (3) own rows: own part plus the halo rows, stored once
     store_own_rows<P>(
         [&](int b) -> T* { return sOff[b][7] >= 0 ? a.Y + (int64_t)sOff[b][7] * kElem16 : nullptr; }, Yp, S, sBase,
-        sLd, U, sHb, sHn, sNode, nb, px, py, pz);
+        sLd, U, sHb, sHn, sNode, sOwn, nb, px, py, pz);
     }  // unit_ok
     else if (tid == 0 && in_mesh) {
         mark_done(a.done, px + a.npx * (py + a.npy * pz));   // a skipped unit: nobody waits for it

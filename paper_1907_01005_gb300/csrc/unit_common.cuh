@@ -208,6 +208,26 @@ __device__ __forceinline__ void fetch_halo(T* hbuf, const T* halo, const int32_t
     }
 }
 
+// Own row r of patch (px, py, pz), rows x fastest over the own range [l, 2p]
+// per direction (l = 0 at coordinate 0, else 1): the node and its own-range
+// coordinates packed as node | rx << 10 | ry << 14 | rz << 18 (built once per
+// work item by own_row_entry, read by store_own_rows).
+template <int P>
+__device__ __forceinline__ int own_row_entry(int r, int px, int py, int pz) {
+    constexpr int Q = 2 * P, NP = 2 * P + 1;
+    const int lx = px > 0, ly = py > 0, lz = pz > 0;
+    // the own range has 2p or 2p + 1 nodes: divisions by constants
+    const int rx = lx ? r % Q : r % (Q + 1), ryz = lx ? r / Q : r / (Q + 1);
+    const int ry = ly ? ryz % Q : ryz % (Q + 1), rz = ly ? ryz / Q : ryz / (Q + 1);
+    const int node = (lx + rx) + NP * ((ly + ry) + NP * (lz + rz));
+    return node | (rx << 10) | (ry << 14) | (rz << 18);
+}
+template <int P>
+__device__ __forceinline__ int own_rows_of(int px, int py, int pz) {
+    constexpr int Q = 2 * P;
+    return (Q + 1 - (px > 0)) * (Q + 1 - (py > 0)) * (Q + 1 - (pz > 0));
+}
+
 // Stores the own rows of every block into Y: the patch's part (the patch
 // tensor yp: node row stride S elements, block b at column colbase[b], ld[b]
 // columns) plus the fetched halo rows of the upper neighbours e within the
@@ -215,32 +235,32 @@ __device__ __forceinline__ void fetch_halo(T* hbuf, const T* halo, const int32_t
 // the row at its halo_face_index), added in the order e = 1 .. 7, so every
 // row has the same rounding on every run; zeros for boundary nodes.  Block
 // b's own rows form one contiguous range of Y starting at own_row0(b) (rows
-// x fastest over the own range), so the threads take its 16-byte chunks in
-// address order and a warp's stores cover consecutive addresses.  Blocks
-// with no own rows here have own_row0(b) == nullptr.
+// x fastest over the own range; own_tab[r] = own_row_entry(r), or nullptr
+// to decode each row where it is used), so the
+// threads take its 16-byte chunks in address order and a warp's stores
+// cover consecutive addresses.  Blocks with no own rows here have
+// own_row0(b) == nullptr.
 template <int P, typename T, typename OwnRow0>
 __device__ __forceinline__ void store_own_rows(OwnRow0 own_row0, const T* yp, int S, const int* colbase,
                                                const int* ld, const T* hbuf, const int (*hb)[8],
-                                               const int (*nslot)[8], const int* node_tab, int nblocks, int px,
-                                               int py, int pz) {
+                                               const int (*nslot)[8], const int* node_tab, const int* own_tab,
+                                               int nblocks, int px, int py, int pz) {
     using V = typename V16<T>::type;
-    constexpr int CH = 16 / sizeof(T), Q = 2 * P, NP = 2 * P + 1;
-    const int lx = px > 0, ly = py > 0, lz = pz > 0;   // own range [l, 2p] per direction
-    const int nx = Q + 1 - lx, ny = Q + 1 - ly, nz = Q + 1 - lz;
-    const int rows = nx * ny * nz;
+    constexpr int CH = 16 / sizeof(T), Q = 2 * P;
+    const int nx = Q + 1 - (px > 0), ny = Q + 1 - (py > 0);
+    const int rows = own_rows_of<P>(px, py, pz);
     for (int b = 0; b < nblocks; ++b) {
         T* yd = own_row0(b);
         if (yd == nullptr) continue;
         const int ldb = ld[b], cpr = ldb / CH, total = rows * cpr;
+        const float inv_cpr = 1.0f / (float)cpr;      // c / cpr exactly for these small c
         int hbe[8];                                    // slot starts, -1 where there is no halo
 #pragma unroll
         for (int e = 1; e < 8; ++e) hbe[e] = nslot[b][e] > 0 ? hb[b][e] : -1;
         for (int c = threadIdx.x; c < total; c += blockDim.x) {
-            const int r = c / cpr, cc = c - r * cpr;
-            // own-range coordinates (2p or 2p + 1 nodes: divisions by constants)
-            const int rx = lx ? r % Q : r % (Q + 1), ryz = lx ? r / Q : r / (Q + 1);
-            const int ry = ly ? ryz % Q : ryz % (Q + 1), rz = ly ? ryz / Q : ryz / (Q + 1);
-            const int node = (lx + rx) + NP * ((ly + ry) + NP * (lz + rz));
+            const int r = __float2int_rz(((float)c + 0.5f) * inv_cpr), cc = c - r * cpr;
+            const int ow = own_tab != nullptr ? own_tab[r] : own_row_entry<P>(r, px, py, pz);
+            const int node = ow & 1023, rx = (ow >> 10) & 15, ry = (ow >> 14) & 15, rz = (ow >> 18) & 15;
             const int ne = node_tab[node];
             V v = V16<T>::zero();
             if (!(ne & kBoundary)) {
