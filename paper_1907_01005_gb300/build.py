@@ -15,7 +15,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libfe_mf.so")
-SOURCES = ["host.cpp", "apply.cu", "apply_unit.cu", "apply_cellmat.cu", "gram.cu", "gram_tc.cu", "mmult.cu", "peak.cu"]
+SOURCES = ["host.cpp", "apply.cu", "apply_unit.cu", "apply_cellmat.cu", "gram.cu", "gram_tc.cu", "mmult.cu", "mmult_tc.cu", "peak.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

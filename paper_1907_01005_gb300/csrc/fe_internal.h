@@ -243,6 +243,17 @@ struct MmultItem {
     int32_t i0, j0;     // first row of the chunk, first union column of the output chunk
     int32_t pad;
 };
+// A stored block as the tensor-core post-multiplication maps it into its row
+// block's padded union: one record per block, in CSR order
+struct MmBlock {
+    int64_t off;        // element offset of the block
+    int32_t u0;         // first padded-union column
+    int32_t ld;         // row stride (padded width)
+    int32_t w;          // width
+    int32_t gcol0;      // first global column
+    int32_t pcol0;      // first padded global column
+    int32_t pad;
+};
 template <typename T>
 struct MmultArgs {
     const T* A;
@@ -261,6 +272,16 @@ struct MmultArgs {
     const int32_t* rb_rows;
     const int32_t* ucol0;       // first padded-union column of each stored block within its row block
     const int32_t* rb_union;    // padded-union columns of each row block
+    // tensor-core path (FP32): padded global columns (each column block at
+    // pcol0[c], ld columns), their global ids (-1 = padding), and X^T in
+    // padded coordinates, split into TF32 high parts and remainders (set by
+    // launch_mmult_tc)
+    const int32_t* pcol0;
+    const int32_t* pglob;
+    const MmBlock* mm_blocks;
+    int32_t n_pcols;
+    const float* XThi;
+    const float* XTlo;
     double alpha, gamma, beta;
     int32_t* status;
 };
@@ -284,6 +305,10 @@ size_t mmult_smem_bytes(int wmax_union);
 constexpr size_t kMmultSmemMax = 200 * 1024;
 template <typename T>
 cudaError_t launch_mmult(const MmultArgs<T>& a, float* x_round, cudaStream_t s);
+// FP32 on the tensor cores (mmult_tc.cu); xt holds 2 n_pcols^2 floats
+size_t mmult_tc_smem_bytes(int wmax_union);
+constexpr size_t kMmultTcSmemMax = 55 * 1024;    // four CTAs per SM
+cudaError_t launch_mmult_tc(const MmultArgs<float>& a, float* xt, cudaStream_t s);
 template <typename T>
 cudaError_t launch_trace(const TraceArgs<T>& a, cudaStream_t s);
 

@@ -58,6 +58,7 @@
 #include <cuda_bf16.h>
 
 #include "fe_internal.h"
+#include "tc_common.cuh"
 
 namespace femf {
 namespace {
@@ -79,61 +80,6 @@ constexpr int kBarProd = 1, kBarEpi = 2, kBarProd1 = 3;  // named barriers: prod
 constexpr int kNone = -30000;             // exponent of an all-zero column
 constexpr int kMaxRows = (2 * kMaxP + 1) * (2 * kMaxP + 1) * (2 * kMaxP + 1);   // rows of a row block
 constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;   // bounded mbarrier waits (0.2 s)
-
-// ---- PTX wrappers -------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: K-major operand, rows of 128 bytes with the
-// 128-byte swizzle, 8-row groups 1024 bytes apart (stride byte offset); the
-// leading byte offset is unused for this layout (one swizzle atom along K).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                 // leading byte offset (16 B, unused)
-    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                 // layout: 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D FP32, A and B bf16, both K-major.
-__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// Waits until the barrier's phase `parity` has completed, for at most
-// `limit_ns`; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-    const uint64_t t0 = global_ns();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
 
 // Tensor-memory loads: thread i of a warp receives lane (32 (warp % 4) + i)
 // of the columns loaded.
@@ -253,10 +199,6 @@ __device__ __forceinline__ int quad_pack(int u, int a0, int ld, int mask, int tc
 __device__ __forceinline__ Quad quad_unpack(int q) {
     return Quad{q & 63, (q >> 6) & 31, (q >> 11) & 255, (q >> 19) & 15, ((q >> 23) & 255) - 4};
 }
-
-// Byte offset of 16-byte chunk j (rows 8j .. 8j+7 of the chunk) of operand
-// row c in a slice panel: the 128-byte swizzle (chunk index XOR row mod 8)
-__device__ __forceinline__ uint32_t sw_off(int c, int j) { return (uint32_t)(c * 128 + ((j ^ (c & 7)) << 4)); }
 
 // Slices 8 values (already multiplied by f1) of operand row c into S bf16
 // slices y_s = q_s 2^(-8 s) on fixed grids, one 16-byte chunk per slice panel.

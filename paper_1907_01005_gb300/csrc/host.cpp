@@ -196,7 +196,10 @@ struct fe_bcsr {
     // post-multiplication and trace (mmult.cu)
     std::vector<MmultItem> mm_items;
     std::vector<int32_t> block_rb, rb_rows, ucol0, rb_union;
+    std::vector<int32_t> pcol0, pglob;  // padded global columns (tensor-core post-multiplication)
+    std::vector<MmBlock> mm_blocks;
     int32_t wmax_union = 0;
+    size_t off_pcol0 = 0, off_pglob = 0, off_mmblocks = 0;
     size_t off_rowptr = 0, off_colidx = 0, off_blkoff = 0, off_blockrb = 0, off_rbrows = 0, off_mmitems = 0;
     size_t off_ucol0 = 0, off_rbunion = 0, off_xround = 0;
     size_t off_tiles = 0, off_epy = 0, off_ipy = 0, off_epp = 0, off_ipp = 0, off_cbp = 0, table_bytes = 0;
@@ -710,6 +713,11 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
             const int w = cbp[cc + 1] - cbp[cc], per16 = 16 / (int)b->elem();
             b->ld[cc] = (w + per16 - 1) / per16 * per16;
         }
+        b->pcol0.assign(ncb + 1, 0);
+        for (int cc = 0; cc < ncb; ++cc) b->pcol0[cc + 1] = b->pcol0[cc] + b->ld[cc];
+        b->pglob.assign(b->pcol0[ncb], -1);
+        for (int cc = 0; cc < ncb; ++cc)
+            for (int q = 0; q < cbp[cc + 1] - cbp[cc]; ++q) b->pglob[b->pcol0[cc] + q] = cbp[cc] + q;
         b->row_ptr.assign(row_ptr, row_ptr + R + 1);
         const int64_t nnz = row_ptr[R];
         b->col_idx.assign(col_idx, col_idx + nnz);
@@ -1002,6 +1010,11 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
                 W += b->ld[col_idx[k]];
             }
             b->rb_union[rr] = W;
+            for (int64_t k = row_ptr[rr]; k < row_ptr[rr + 1]; ++k) {
+                const int c = col_idx[k];
+                b->mm_blocks.push_back(MmBlock{b->blk_off[k], b->ucol0[k], b->ld[c], cbp[c + 1] - cbp[c], cbp[c],
+                                               b->pcol0[c], 0});
+            }
             b->wmax_union = std::max(b->wmax_union, W);
             for (int i0 = 0; W > 0 && i0 < rows; i0 += 64)
                 for (int j0 = 0; j0 < W; j0 += 128) b->mm_items.push_back(MmultItem{rr, i0, j0, 0});
@@ -1042,8 +1055,14 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
         b->off_mmitems = off; off = align_up(off + b->mm_items.size() * sizeof(MmultItem), 256);
         b->off_ucol0 = off; off = align_up(off + std::max<int64_t>(nnz, 1) * sizeof(int32_t), 256);
         b->off_rbunion = off; off = align_up(off + R * sizeof(int32_t), 256);
-        // X of fe_mmult rounded to FP32 (FE_F32 multivectors)
-        b->off_xround = off; off = align_up(off + (dtype == FE_F32 ? (size_t)n_cols * n_cols * sizeof(float) : 16), 256);
+        // X of fe_mmult in FP32 (FE_F32 multivectors): rounded, or (tensor-core
+        // path) transposed into padded columns and split in two
+        b->off_pcol0 = off; off = align_up(off + b->pcol0.size() * sizeof(int32_t), 256);
+        b->off_mmblocks = off; off = align_up(off + std::max<size_t>(b->mm_blocks.size(), 1) * sizeof(MmBlock), 256);
+        b->off_pglob = off; off = align_up(off + std::max<size_t>(b->pglob.size(), 1) * sizeof(int32_t), 256);
+        const size_t np = b->pglob.size();
+        b->off_xround = off;
+        off = align_up(off + (dtype == FE_F32 ? std::max((size_t)n_cols * n_cols, 2 * np * np) * sizeof(float) : 16), 256);
         b->table_bytes = off;
     } catch (const std::bad_alloc&) {
         delete b;
@@ -1127,6 +1146,10 @@ int fe_bcsr_bind(fe_bcsr* b, void* values, void* tables, void* stream) {
         FE_TRY_CUDA(put(b->off_mmitems, b->mm_items.data(), b->mm_items.size() * sizeof(MmultItem)), "fe_bcsr_bind: mmult items");
         FE_TRY_CUDA(put(b->off_ucol0, b->ucol0.data(), b->ucol0.size() * sizeof(int32_t)), "fe_bcsr_bind: union");
         FE_TRY_CUDA(put(b->off_rbunion, b->rb_union.data(), b->rb_union.size() * sizeof(int32_t)), "fe_bcsr_bind: union");
+        FE_TRY_CUDA(put(b->off_pcol0, b->pcol0.data(), b->pcol0.size() * sizeof(int32_t)), "fe_bcsr_bind: padded columns");
+        FE_TRY_CUDA(put(b->off_mmblocks, b->mm_blocks.data(), b->mm_blocks.size() * sizeof(MmBlock)),
+                    "fe_bcsr_bind: block records");
+        FE_TRY_CUDA(put(b->off_pglob, b->pglob.data(), b->pglob.size() * sizeof(int32_t)), "fe_bcsr_bind: padded columns");
         // the source arrays are members of the handle; make sure the copies
         // are done before a later re-bind could free them
         FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_bcsr_bind: synchronize");
@@ -1520,8 +1543,20 @@ int mmult_impl(const fe_bcsr* A, const double* X, double alpha, double gamma, do
     a.alpha = alpha;
     a.gamma = gamma;
     a.beta = beta;
+    a.pcol0 = reinterpret_cast<const int32_t*>(t + C->off_pcol0);
+    a.pglob = reinterpret_cast<const int32_t*>(t + C->off_pglob);
+    a.mm_blocks = reinterpret_cast<const MmBlock*>(t + C->off_mmblocks);
+    a.n_pcols = (int32_t)C->pglob.size();
+    a.XThi = a.XTlo = nullptr;
     a.status = A->mesh ? A->mesh->status : nullptr;
     float* x_round = reinterpret_cast<float*>(static_cast<char*>(C->tables) + C->off_xround);
+    if constexpr (sizeof(T) == 4) {
+        // the tensor cores where the row blocks' unions fit the tables of two CTAs per SM
+        if (mmult_tc_smem_bytes(a.wmax_union) <= kMmultTcSmemMax) {
+            FE_TRY_CUDA(launch_mmult_tc(a, x_round, s), "fe_mmult: tensor-core kernel launch");
+            return FE_OK;
+        }
+    }
     FE_TRY_CUDA(launch_mmult<T>(a, x_round, s), "fe_mmult: kernel launch");
     return FE_OK;
 }
