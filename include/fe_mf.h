@@ -316,8 +316,8 @@ int fe_trace_dot(const fe_bcsr* D, const fe_bcsr* G, double* out_dev, void* stre
 /* ------------------------------------------------------------------------
  * Launch configuration, CUDA graph of the step, autotuner.  These shape how
  * the kernels of Alg. 6 / Alg. 8 are launched on this GPU; the paper's method
- * is unchanged by them (results are identical up to the order of the FP
- * additions in the scatter).
+ * is unchanged by them (Y is bit-identical under every launch shape; the Gram
+ * products change only in the order of their FP64 additions).
  * ------------------------------------------------------------------------ */
 
 /* Launch knobs of fe_apply_H for source multivector P:
@@ -330,6 +330,16 @@ int fe_trace_dot(const fe_bcsr* D, const fe_bcsr* G, double* out_dev, void* stre
  *                   patch a CTA holds at once (used by the p >= 3 kernel only).
  * Defaults: 0, 4, 0.  FE_EINVAL for values outside these ranges. */
 int fe_bcsr_set_launch(fe_bcsr* P, int32_t persistent, int32_t ctas_per_sm, int32_t cells_per_round);
+
+/* Caps the SMs that the persistent launches reading P may occupy: the
+ * tensor-core Gram products (fe_gram_*, with P as A), the persistent apply
+ * (fe_apply_H / fe_apply_M with P as source) and the tensor-core
+ * post-multiplication (fe_mmult with P as A) launch at most max_sms SMs'
+ * worth of CTAs.  0 (the default) = every SM.  Other streams' kernels then
+ * find SMs free while these run (a server gives its large requests a cap and
+ * its small ones the rest).  Results are unchanged.  FE_EINVAL for
+ * max_sms < 0. */
+int fe_bcsr_set_sm_limit(fe_bcsr* P, int32_t max_sms);
 int fe_bcsr_get_launch(const fe_bcsr* P, int32_t* persistent, int32_t* ctas_per_sm,
                        int32_t* cells_per_round);
 

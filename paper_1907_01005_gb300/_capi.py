@@ -91,6 +91,7 @@ SIGNATURES = {
     "fe_mmult": [_P, _P, _dbl, _dbl, _dbl, _P, _P],
     "fe_trace_dot": [_P, _P, _P, _P],
     "fe_bcsr_set_launch": [_P, _i32, _i32, _i32],
+    "fe_bcsr_set_sm_limit": [_P, _i32],
     "fe_bcsr_get_launch": [_P, _pi32, _pi32, _pi32],
     "fe_bcsr_set_closed": [_P, _i32],
     "fe_bcsr_get_closed": [_P, _pi32],

@@ -183,6 +183,10 @@ class BCSR:
     def set_launch(self, persistent: int, ctas_per_sm: int = 4, cells_per_round: int = 0):
         check(capi.fe_bcsr_set_launch(self.h, int(persistent), int(ctas_per_sm), int(cells_per_round)))
 
+    def set_sm_limit(self, max_sms: int):
+        """Caps the SMs of the persistent launches reading this multivector (0: all)."""
+        check(capi.fe_bcsr_set_sm_limit(self.h, int(max_sms)))
+
     def set_closed(self, closed: bool):
         """Declares the pattern closed for P's values (P^T Y is then symmetric)."""
         check(capi.fe_bcsr_set_closed(self.h, 1 if closed else 0))

@@ -409,9 +409,8 @@ cudaError_t launch_cellmat_p(const CellMatArgs& a, cudaStream_t s) {
         attr = true;
     }
     if (a.n_units == 0) return cudaSuccess;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = usable_sms(a.sm_limit);
+    if (sms < 1) return cudaErrorInvalidDevice;
     const unsigned grid = (unsigned)std::min<int64_t>(a.n_units, (int64_t)sms * 2);
     if (a.mass)
         apply_cellmat_kernel<P, true><<<grid, G::THREADS, G::bytes, s>>>(a);

@@ -338,9 +338,8 @@ cudaError_t launch_units_p(const ApplyUnitArgs<T>& a, cudaStream_t s) {
     if (a.n_units == 0) return cudaSuccess;
     unsigned grid = (unsigned)a.n_units;
     if (a.persistent) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int sms = usable_sms(a.sm_limit);
+        if (sms < 1) return cudaErrorInvalidDevice;
         grid = (unsigned)std::min<int64_t>(a.n_units, (int64_t)sms * std::max(1, a.ctas_per_sm));
     }
     if (a.mass)

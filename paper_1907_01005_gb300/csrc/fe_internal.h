@@ -126,6 +126,7 @@ struct GramTcArgs {
     const int32_t* col_glob;    // global column id
     const int32_t* rows;        // rows of each row block
     int16_t* item_exp;          // scratch: item exponents, 2 x gram_tc_tile() per item (A side, B side)
+    int32_t sm_limit;           // > 0: the persistent kernel runs on at most this many SMs
     int32_t n_cols;
     double* G;
     int32_t* status;            // device status word (set on a malformed work item)
@@ -134,6 +135,8 @@ struct GramTcArgs {
 // known to be symmetric (closed pattern), upper super-tiles, mirrored
 enum class GramMode { PtY = 0, PtP = 1, PtYSym = 2 };
 cudaError_t launch_gram_tc(const GramTcArgs& a, GramMode mode, cudaStream_t s);
+// SMs a persistent launch may occupy: the device's, capped by sm_limit > 0
+int usable_sms(int32_t sm_limit);
 int gram_tc_tile();         // output tile edge of the tensor-core Gram (union columns)
 int gram_tc_item_rows(bool pp);   // most rows of a work item of P^T P (pp) or P^T Y
 
@@ -188,6 +191,7 @@ struct ApplyUnitArgs {
     unsigned long long* ticket;   // work counter (zeroed before the launch): units go in descending order
     int32_t persistent;           // 1: ctas_per_sm CTAs per SM loop over the work counter; 0: a CTA per unit
     int32_t ctas_per_sm;
+    int32_t sm_limit;             // > 0: the persistent launch occupies at most this many SMs' worth
     int32_t* done;                // units per patch whose halo is written (zeroed before the launch), by patch id
     const int32_t* count;         // units per patch, indexed by patch id
     T* halo;                      // halo region (Unit.hout / hin offsets)
@@ -227,6 +231,7 @@ struct CellMatArgs {
     int32_t* status;
     int32_t mass;                 // 1: the mass operator (stage 1 only, Vq unused)
     const float* consts;          // the operator's constant set (16-byte aligned, device)
+    int32_t sm_limit;             // > 0: at most this many SMs' worth of persistent CTAs
 };
 cudaError_t launch_apply_cellmat(int p, const CellMatArgs& a, cudaStream_t s);
 template <typename T>
@@ -282,6 +287,7 @@ struct MmultArgs {
     int32_t n_pcols;
     const float* XThi;
     const float* XTlo;
+    int32_t sm_limit;           // > 0: at most this many SMs' worth of persistent CTAs (tensor-core path)
     double alpha, gamma, beta;
     int32_t* status;
 };

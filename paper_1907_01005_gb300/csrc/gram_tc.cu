@@ -739,13 +739,11 @@ cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
         attr = true;
     }
     if (g.n_items == 0) return cudaSuccess;
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
+    const int sms = usable_sms(g.sm_limit);
+    if (sms < 1) return cudaErrorInvalidDevice;
     // the item exponents first (one CTA per item), then the persistent kernel
     gram_exp_kernel<SYM, SAME, ROWS><<<(unsigned)g.n_items, kGroupThreads, 0, s>>>(g);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<int64_t>(g.n_items, (int64_t)sms);
     gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW><<<grid, kThreads, smem, s>>>(g);

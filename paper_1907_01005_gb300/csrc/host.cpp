@@ -216,6 +216,7 @@ struct fe_bcsr {
     size_t off_halo = 0;
     // launch configuration of the apply (set by fe_bcsr_set_launch / fe_autotune)
     int32_t persistent = 0, ctas_per_sm = 4, cells_per_round = 0;
+    int32_t sm_limit = 0;   // SMs the persistent launches reading this multivector may occupy (0: all)
     int32_t closed = 0;   // the caller declares the pattern closed for P's values (fe_bcsr_set_closed)
     int32_t form = 0;     // FE_FORM_SUMFAC or FE_FORM_CELLMAT (fe_bcsr_set_form)
     int64_t active_cell_cols = 0;
@@ -225,6 +226,7 @@ struct fe_bcsr {
     void* tables = nullptr;
     // side stream of fe_apply_H_gram (P^T P runs beside the apply), created on first use
     cudaStream_t side = nullptr;
+    int side_prio = 0;    // its priority: the caller stream's at creation
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t elem() const { return dtype == FE_F64 ? 8 : 4; }
     // copy stream of fe_apply_H_gram_host (Y goes back to the host while P^T Y runs)
@@ -1243,6 +1245,7 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool ma
             c.lx = a.lx; c.ly = a.ly; c.lz = a.lz; c.dirichlet = a.dirichlet;
             c.status = a.status;
             c.mass = a.mass;
+            c.sm_limit = P->sm_limit;
             c.consts = reinterpret_cast<const float*>(static_cast<const char*>(m->ws) + 256) +
                        (mass ? cellmat_set_floats(m->p) : 0);
             FE_TRY_CUDA(launch_apply_cellmat(m->p, c, s), "fe_apply_H: cell-matrix kernel launch");
@@ -1257,6 +1260,7 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool ma
         u.ticket = ticket;
         u.persistent = P->persistent;
         u.ctas_per_sm = P->ctas_per_sm;
+        u.sm_limit = P->sm_limit;
         u.done = done;
         u.count = ucount;
         u.halo = halo;
@@ -1281,6 +1285,17 @@ int apply_impl(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, cudaStream_t s, bool ma
     return FE_OK;
 }
 
+}  // namespace
+
+int femf::usable_sms(int32_t sm_limit) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sm_limit > 0 ? std::min(sms, (int)sm_limit) : sms;
+}
+
+namespace {
+
 int gram_tc_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaStream_t s) {
     GramTcArgs g;
     const char* t = static_cast<const char*>(A->tables);
@@ -1296,6 +1311,7 @@ int gram_tc_impl(const fe_bcsr* A, const fe_bcsr* B, bool sym, double* G, cudaSt
     g.col_glob = reinterpret_cast<const int32_t*>(t + A->off_tccg);
     g.rows = reinterpret_cast<const int32_t*>(t + A->off_tcrows);
     g.item_exp = reinterpret_cast<int16_t*>(const_cast<char*>(t) + (pp ? A->off_tcexp_pp : A->off_tcexp_py));
+    g.sm_limit = A->sm_limit;
     g.n_cols = A->n_cols;
     g.G = G;
     g.status = A->mesh ? A->mesh->status : nullptr;
@@ -1384,10 +1400,21 @@ int fe_gram_PtP(const fe_bcsr* P, double* G, void* stream) {
 }
 
 namespace {
-// P's side stream and its fork/join events, created on first use
-int ensure_side(fe_bcsr* Pm) {
+// P's side stream and its fork/join events, created on first use; the side
+// stream takes the priority of the caller's stream (it is created again when
+// that changes: a server runs small requests on high-priority streams)
+int ensure_side(fe_bcsr* Pm, cudaStream_t caller) {
+    int prio = 0;
+    FE_TRY_CUDA(cudaStreamGetPriority(caller, &prio), "fe_apply_H_gram: stream priority");
+    if (Pm->side && Pm->side_prio != prio) {
+        FE_TRY_CUDA(cudaStreamDestroy(Pm->side), "fe_apply_H_gram: side stream");   // its work still completes
+        Pm->side = nullptr;
+    }
     if (!Pm->side) {
-        FE_TRY_CUDA(cudaStreamCreateWithFlags(&Pm->side, cudaStreamNonBlocking), "fe_apply_H_gram: side stream");
+        FE_TRY_CUDA(cudaStreamCreateWithPriority(&Pm->side, cudaStreamNonBlocking, prio), "fe_apply_H_gram: side stream");
+        Pm->side_prio = prio;
+    }
+    if (!Pm->ev_fork) {
         FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_fork, cudaEventDisableTiming), "fe_apply_H_gram: event");
         FE_TRY_CUDA(cudaEventCreateWithFlags(&Pm->ev_join, cudaEventDisableTiming), "fe_apply_H_gram: event");
     }
@@ -1401,9 +1428,9 @@ int fe_apply_H_gram(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY, doub
     // P^T P does not depend on Y: it runs on P's side stream, forked from and
     // joined back into `stream` with events (a pattern stream capture keeps)
     fe_bcsr* Pm = const_cast<fe_bcsr*>(P);
-    rc = ensure_side(Pm);
-    if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    rc = ensure_side(Pm, s);
+    if (rc) return rc;
     FE_TRY_CUDA(cudaEventRecord(Pm->ev_fork, s), "fe_apply_H_gram: fork");
     FE_TRY_CUDA(cudaStreamWaitEvent(Pm->side, Pm->ev_fork, 0), "fe_apply_H_gram: fork");
     const int rc_pp = fe_gram_PtP(P, G_PP, Pm->side);
@@ -1422,7 +1449,7 @@ int fe_apply_H_gram_host(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY,
     int rc = check_pair("fe_apply_H_gram_host", m, P, Y);
     if (rc) return rc;
     fe_bcsr* Pm = const_cast<fe_bcsr*>(P);
-    rc = ensure_side(Pm);
+    rc = ensure_side(Pm, (cudaStream_t)stream);
     if (rc) return rc;
     if (!Pm->copy) {
         FE_TRY_CUDA(cudaStreamCreateWithFlags(&Pm->copy, cudaStreamNonBlocking), "fe_apply_H_gram_host: copy stream");
@@ -1500,6 +1527,13 @@ int fe_bcsr_set_launch(fe_bcsr* b, int32_t persistent, int32_t ctas_per_sm, int3
     return FE_OK;
 }
 
+int fe_bcsr_set_sm_limit(fe_bcsr* b, int32_t max_sms) {
+    if (!b) return fail(FE_EINVAL, "fe_bcsr_set_sm_limit: NULL multivector");
+    if (max_sms < 0) return fail(FE_EINVAL, "fe_bcsr_set_sm_limit: max_sms >= 0 (0: every SM)");
+    b->sm_limit = max_sms;
+    return FE_OK;
+}
+
 int fe_bcsr_set_form(fe_bcsr* b, int32_t form) {
     if (!b) return fail(FE_EINVAL, "fe_bcsr_set_form: NULL multivector");
     if (form != FE_FORM_SUMFAC && form != FE_FORM_CELLMAT)
@@ -1546,6 +1580,7 @@ int mmult_impl(const fe_bcsr* A, const double* X, double alpha, double gamma, do
     a.pcol0 = reinterpret_cast<const int32_t*>(t + C->off_pcol0);
     a.pglob = reinterpret_cast<const int32_t*>(t + C->off_pglob);
     a.mm_blocks = reinterpret_cast<const MmBlock*>(t + C->off_mmblocks);
+    a.sm_limit = A->sm_limit;
     a.n_pcols = (int32_t)C->pglob.size();
     a.XThi = a.XTlo = nullptr;
     a.status = A->mesh ? A->mesh->status : nullptr;

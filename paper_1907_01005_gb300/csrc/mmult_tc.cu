@@ -282,10 +282,8 @@ cudaError_t launch_mmult_tc(const MmultArgs<float>& a, float* xt, cudaStream_t s
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
+    const int sms = usable_sms(a.sm_limit);
+    if (sms < 1) return cudaErrorInvalidDevice;
     const unsigned grid = (unsigned)std::min<int64_t>(a.n_items, kTcCtasPerSm * (int64_t)sms);
     mmult_tc_kernel<<<grid, kTcThreads, smem, s>>>(b);
     return cudaGetLastError();

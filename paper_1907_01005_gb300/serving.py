@@ -18,8 +18,12 @@ DoF x column count), except that a request which has waited more than
 goes ahead of all unaged ones, in arrival order, so large requests cannot
 starve.  The last free slot is kept for small requests (predicted at most
 the median of the registered payloads) unless the request is aged, so that
-small requests do not queue behind a GPU full of large ones.  Requests that
-arrive while others run join them on the device: each
+small requests do not queue behind a GPU full of large ones.  On the
+device, small requests run on high-priority streams (their CTAs are
+scheduled before the pending CTAs of large ones), and the persistent kernels
+of large requests are capped to all but `reserve_sms` SMs, so that a small
+request finds SMs free while a large request's Gram products run.  Requests
+that arrive while others run join them on the device: each
 admitted request runs `fe_apply_H_gram` on its own CUDA stream and the
 kernels of different requests overlap.  A request completes when its Gram
 matrices (and, if asked, Y) are back in host memory; its latency is measured
@@ -91,14 +95,22 @@ class Server:
     """Continuous-batching server on one GPU (see the module docstring)."""
 
     def __init__(self, budget_bytes: int | None = None, slots: int = 4, device: str = "cuda",
-                 age_factor: float = 4.0, min_age_s: float = 2e-3, seed_rate: float = 1e11):
+                 age_factor: float = 4.0, min_age_s: float = 2e-3, seed_rate: float = 1e11,
+                 reserve_sms: int = 16, priority_small: bool = True):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         free, _total = torch.cuda.mem_get_info(self.device)
         self.budget = int(budget_bytes if budget_bytes is not None else 0.8 * free)
         self.slots = slots
+        # per slot a normal stream (large requests) and a high-priority one
+        # (small requests: their CTAs are scheduled ahead of pending large ones)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.streams_hi = [torch.cuda.Stream(device=self.device, priority=-8) for _ in range(slots)]
+        n_sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        # large requests' persistent kernels leave reserve_sms SMs to the small ones
+        self.large_sm_limit = max(1, n_sms - reserve_sms) if reserve_sms > 0 else 0
+        self.priority_small = priority_small
         self.free_streams = list(range(slots))
         self.payloads: dict[int, Payload] = {}
         self.meshes: dict[tuple, dict] = {}       # mesh key -> {"mesh": Mesh, "bytes": int, "users": set}
@@ -213,8 +225,10 @@ class Server:
         pl = self.payloads[r.pid]
         pb = pl.problem
         si = self.free_streams.pop()
-        s = self.streams[si]
+        small = pl.service_s <= self.small_s
+        s = self.streams_hi[si] if small and self.priority_small else self.streams[si]
         r.stream = si
+        pb.P.set_sm_limit(0 if small else self.large_sm_limit)
         d = pl.dev
         with torch.cuda.stream(s):
             if r.p_host is not None:
