@@ -16,9 +16,9 @@
 // (hi = TF32 rounding, lo = the FP32 remainder): about 2^-21 relative per
 // product, inside the FP32 tolerance of C.
 //
-// Operands.  X is transposed, rounded to FP32, split, and laid out in padded
-// global coordinates once per call (round_xt_kernel): XT[pv][pu] = X[u][v],
-// zero for padding columns.  A panel row of X^T (an output column v) over a
+// Operands.  X + gamma I is transposed, rounded to FP32, split, and laid out
+// in padded global coordinates once per call (round_xt_kernel): XT[pv][pu] =
+// (X + gamma I)[u][v], zero for padding columns (the gamma term rides on X).  A panel row of X^T (an output column v) over a
 // K chunk is then 16-byte copies from one row of XT, straight into the
 // swizzled tile (cp.async).  A is read with 16-byte loads, split in
 // registers, and stored swizzled.  One 48 KB stage per CTA, so that four
@@ -58,17 +58,19 @@ __device__ __forceinline__ void cp_async16z(uint32_t dst, const void* src, bool 
                  : "memory");
 }
 
-// XT[pv][pu] = X[pglob[pu]][pglob[pv]] rounded to FP32 and split into a TF32
-// high part and the FP32 remainder; zero where either padded column is
-// padding (pglob < 0).
+// XT[pv][pu] = (X + gamma I)[pglob[pu]][pglob[pv]] rounded to FP32 and split
+// into a TF32 high part and the FP32 remainder; zero where either padded
+// column is padding (pglob < 0).  On a row block's union A (X + gamma I) =
+// A X + gamma A, so the gamma term needs no second read of A.
 __global__ void __launch_bounds__(256) round_xt_kernel(const double* __restrict__ X, const int32_t* __restrict__ pglob,
-                                                       int n_pcols, int n_cols, float* __restrict__ xt_hi,
+                                                       int n_pcols, int n_cols, double gamma, float* __restrict__ xt_hi,
                                                        float* __restrict__ xt_lo) {
     const int64_t total = (int64_t)n_pcols * n_pcols;
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < total; i += (int64_t)gridDim.x * 256) {
         const int pv = (int)(i / n_pcols), pu = (int)(i - (int64_t)pv * n_pcols);
         const int gu = pglob[pu], gv = pglob[pv];
-        const float x = (gu >= 0 && gv >= 0) ? (float)X[(int64_t)gu * n_cols + gv] : 0.f;
+        const float x =
+            (gu >= 0 && gv >= 0) ? (float)(X[(int64_t)gu * n_cols + gv] + (gu == gv ? gamma : 0.0)) : 0.f;
         const float h = tf32_hi(x);
         xt_hi[i] = h;
         xt_lo[i] = x - h;
@@ -215,13 +217,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) mmult_tc_kernel(cons
         if (sFail) break;
         tc_fence_after();
 
-        // ---- C = alpha (A X + gamma A) + beta C; padding columns written as zero --
+        // ---- C = alpha A (X + gamma I) + beta C; padding columns written as zero --
         const int q = warp & 3, h = warp >> 2;
         const int uo = it.j0 + 32 * q + lane;     // this thread's output union column
         float acc[32];
         tmem_load<32>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), acc);
         if (uo < W) {
-            const float alpha = (float)a.alpha, gamma = (float)a.gamma, beta = (float)a.beta;
+            const float alpha = (float)a.alpha, beta = (float)a.beta;
             const int64_t ou = sUoff[uo];
             const int ldu = sUld[uo];
             const bool pad = sUcol[uo] < 0;
@@ -232,9 +234,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) mmult_tc_kernel(cons
                 const int64_t o = ou + (int64_t)row * ldu;
                 float v = 0.f;
                 if (!pad) {
-                    v = acc[i];
-                    if (gamma != 0.f) v = fmaf(gamma, a.A[o], v);
-                    v *= alpha;
+                    v = alpha * acc[i];
                     if (beta != 0.f) v = fmaf(beta, a.C[o], v);
                 }
                 a.C[o] = v;
@@ -273,7 +273,7 @@ cudaError_t launch_mmult_tc(const MmultArgs<float>& a, float* xt, cudaStream_t s
     b.XThi = xt;
     b.XTlo = xt + n;
     round_xt_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 2048), 256, 0, s>>>(a.X, a.pglob, a.n_pcols,
-                                                                                     a.n_cols, xt, xt + n);
+                                                                                     a.n_cols, a.gamma, xt, xt + n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     static bool attr = false;
