@@ -309,14 +309,14 @@ def load_bf16_peak():
 # ncu capture of the FP32 p2 workload (profiles/*_p2_f32.md), with the SHA-256
 # of the kernel's source files at capture time; reported only while those
 # sources are unchanged.
-_SRC_GRAM = ("gram_tc.cu",)
+_SRC_GRAM = ("gram_tc.cu", "tc_common.cuh")
 _SRC_APPLY = ("apply_unit.cu", "unit_common.cuh")
-_SRC_MMULT = ("mmult.cu",)
+_SRC_MMULT = ("mmult_tc.cu", "tc_common.cuh")
 NCU_TRAFFIC = {
-    "gram_py": (_SRC_GRAM, "78e17e1c22840b51c1d9803fcb618979de9234a529c23c5e4cc0ab58c954ebfb", 506702080),
-    "gram_pp": (_SRC_GRAM, "78e17e1c22840b51c1d9803fcb618979de9234a529c23c5e4cc0ab58c954ebfb", 256430848),
-    "apply": (_SRC_APPLY, "1bc773a6ea92c9c0e9577d57bd3794cc843d694a80dbe30c5f744119779ed9bc", 655558912),
-    "mmult": (_SRC_MMULT, "1ba37459ab68dc9c047f3d4afc08675456773d90c7df21aa698aea12cea384b5", 706672384),
+    # P^T Y (symmetric form) and P^T P (diagonal + off-diagonal tiles)
+    "gram_py": (_SRC_GRAM, "aadc0a7a6e36453952ad4bf74bcb7745a2158160d3a2599b82d6245f570c4385", 513266432),
+    "gram_pp": (_SRC_GRAM, "aadc0a7a6e36453952ad4bf74bcb7745a2158160d3a2599b82d6245f570c4385", 280160768),
+    "apply": (_SRC_APPLY, "dcc43559e402f7a95e266b012ea5ce4ed2b7bb1a70b25ce53a6455d603070966", 730593536),
 }
 
 
