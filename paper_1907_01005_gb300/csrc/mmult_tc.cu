@@ -220,24 +220,31 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) mmult_tc_kernel(cons
         // ---- C = alpha A (X + gamma I) + beta C; padding columns written as zero --
         const int q = warp & 3, h = warp >> 2;
         const int uo = it.j0 + 32 * q + lane;     // this thread's output union column
-        float acc[32];
-        tmem_load<32>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), acc);
-        if (uo < W) {
-            const float alpha = (float)a.alpha, beta = (float)a.beta;
-            const int64_t ou = sUoff[uo];
-            const int ldu = sUld[uo];
-            const bool pad = sUcol[uo] < 0;
+        const float alpha = (float)a.alpha, beta = (float)a.beta;
+        const bool col_ok = uo < W;
+        const int64_t ou = col_ok ? sUoff[uo] : 0;
+        const int ldu = col_ok ? sUld[uo] : 0;
+        const bool pad = !col_ok || sUcol[uo] < 0;
+        // 16 rows of accumulator columns at a time (a warp-wide load); then, 8
+        // rows at a time, all the loads of C before the stores, so that the
+        // loads are not held behind the stores to the same array
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int row = it.i0 + 32 * h + i;
-                if (row >= rows) continue;
-                const int64_t o = ou + (int64_t)row * ldu;
-                float v = 0.f;
-                if (!pad) {
-                    v = alpha * acc[i];
-                    if (beta != 0.f) v = fmaf(beta, a.C[o], v);
+        for (int i0 = 0; i0 < 32; i0 += 16) {
+            float acc[16];
+            tmem_load<16>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h + i0), acc);
+            if (col_ok) {
+#pragma unroll
+                for (int i1 = 0; i1 < 16; i1 += 8) {
+                    const int row0 = it.i0 + 32 * h + i0 + i1;
+                    float* c0 = a.C + ou + (int64_t)row0 * ldu;
+                    float cv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        cv[i] = (beta != 0.f && !pad && row0 + i < rows) ? c0[(int64_t)i * ldu] : 0.f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (row0 + i < rows) c0[(int64_t)i * ldu] = pad ? 0.f : fmaf(beta, cv[i], alpha * acc[i1 + i]);
                 }
-                a.C[o] = v;
             }
         }
         tc_fence_before();
