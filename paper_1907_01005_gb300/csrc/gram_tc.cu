@@ -50,8 +50,10 @@
 //                        warp w reaches lanes 32 (w % 4) .. + 31 and takes
 //                        half of the tile's columns), releases them, and
 //                        adds the results into G.
-// P^T Y keeps two accumulator sets in tensor memory, so the epilogue of an
-// item overlaps the MMAs of the next; P^T P (four classes) has one.  Every
+// The tensor memory holds two accumulator sets of 256 columns: P^T Y (two
+// classes) always uses one, alternating, so the epilogue of an item overlaps
+// the MMAs of the next; so do the P^T P diagonal tiles with N <= 64 (four
+// classes of 64 columns); wider P^T P tiles take both.  Every
 // mbarrier wait is bounded in time: on a time-out the kernel sets the status
 // word, and every role leaves its loop; the MMA issuer waits (bounded) for its
 // MMAs in flight before the tensor memory is freed.
@@ -84,11 +86,11 @@ constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;   // bounded mbarrier wa
 // Tensor-memory loads: thread i of a warp receives lane (32 (warp % 4) + i)
 // of the columns loaded.
 // The NCLS level classes of 8 consecutive columns: NCLS loads of 32 lanes x 8
-// columns (column col + k kST for class k), then one wait.  The wait (and an
+// columns (column col + k cstride for class k), then one wait.  The wait (and an
 // empty statement for the second half of the registers) is tied to the
 // destination registers so that no use moves above it.
 template <int NCLS>
-__device__ __forceinline__ void tmem_load_classes(uint32_t taddr, float (&v)[NCLS][8]) {
+__device__ __forceinline__ void tmem_load_classes(uint32_t taddr, uint32_t cstride, float (&v)[NCLS][8]) {
     static_assert(NCLS == 2 || NCLS == 4, "two or four level classes");
     uint32_t r[NCLS][8];
 #pragma unroll
@@ -96,7 +98,7 @@ __device__ __forceinline__ void tmem_load_classes(uint32_t taddr, float (&v)[NCL
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                      : "=r"(r[k][0]), "=r"(r[k][1]), "=r"(r[k][2]), "=r"(r[k][3]), "=r"(r[k][4]), "=r"(r[k][5]),
                        "=r"(r[k][6]), "=r"(r[k][7])
-                     : "r"(taddr + (uint32_t)(k * kST)));
+                     : "r"(taddr + (uint32_t)k * cstride));
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[0][4]), "+r"(r[0][5]),
                    "+r"(r[0][6]), "+r"(r[0][7]), "+r"(r[1][0]), "+r"(r[1][1]), "+r"(r[1][2]), "+r"(r[1][3]),
@@ -317,6 +319,37 @@ struct ItemMeta {
     int E[2][kST];
 };
 
+// Tensor-memory accumulators: two halves of 256 columns.  An item whose NCLS
+// level classes of cs columns each fit in a half (cs = 64 for P^T P diagonal
+// tiles with N <= 64, otherwise 128) takes one half, the halves alternating,
+// so its MMAs overlap the epilogue of the item before; a wider item takes
+// both.  The MMA issuer and the epilogue walk the items in the same order and
+// keep the same per-half use counts, which give the mbarrier phases.
+struct AccState {
+    int hnext;
+    int uses[2];
+};
+struct AccPlan {
+    int h0, nh, cs;       // halves h0 .. h0 + nh - 1, class stride in columns
+    uint32_t base;        // first tensor-memory column
+};
+template <int NCLS, bool HALF>
+__device__ __forceinline__ AccPlan acc_plan(AccState& st, int N) {
+    AccPlan p;
+    p.cs = (HALF && N <= kST / 2) ? kST / 2 : kST;
+    if (NCLS * p.cs <= 256) {
+        p.h0 = st.hnext;
+        p.nh = 1;
+        st.hnext ^= 1;
+    } else {
+        p.h0 = 0;
+        p.nh = 2;
+        st.hnext = 0;
+    }
+    p.base = 256u * (uint32_t)p.h0;
+    return p;
+}
+
 // Tables of one item for a group of 256 producer threads (8 warps): the
 // group's row-block offsets and row prefix, the tile's columns and their
 // 16-byte quads, and the normalisation factors of the columns.
@@ -426,7 +459,7 @@ __global__ void __launch_bounds__(kGroupThreads) gram_exp_kernel(const GramTcArg
 // highest level kept; NCLS level classes; SYM upper tiles mirrored; NAT the
 // natural three-slice split; NST ring stages (2: a chunk in one 96 KB stage;
 // 1: the two operands of a P^T P off-diagonal chunk across the whole 192 KB)
-template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS, int PW>
+template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS, int PW, bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g) {
     static_assert(!NAT || (SA == 3 && SB == 3), "natural slices: three per operand");
     static_assert(PW == 8 || PW == 16, "one or two producer groups");
@@ -434,7 +467,6 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
     constexpr int kProdThreads = 32 * PW, kEpiThreads = 32 * EW;
     constexpr int kEpiCols = kST / (EW / 4);                   // tile columns of an epilogue warp
     static_assert(NCLS * kST <= 512, "tensor memory: 128 columns per level class");
-    constexpr int NSETS = 512 / (NCLS * kST);   // accumulator sets in tensor memory
     constexpr int U = 8 * LMAX;                 // the epilogue works in units of 2^-U
     constexpr int bytesA = SA * kPanel, bytesB = SB * kPanel;
     static_assert(NST == 2 ? (SAME ? bytesA : bytesA + bytesB) <= kStage : bytesA + bytesB <= 2 * kStage,
@@ -581,23 +613,25 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
         const int m = 32 * quad + lane;                   // tile row (A column) of this thread
         const int part = ew >> 2;                         // tile columns [kEpiCols part, + kEpiCols)
         const int etid = tid - kProdThreads;
+        AccState est{0, {0, 0}};
         for (int64_t item = blockIdx.x, il = 0; item < g.n_items; item += gridDim.x, ++il) {
             const GramTcItem it = g.items[item];
             const GramTcGroup gr = g.groups[it.group];
             const ItemGeo ig = item_geo<SYM, SAME, ROWS>(it, gr);
             if (!ig.ok) continue;
-            const int set = (int)(il % NSETS), slot = (int)(il & 1);
+            const int slot = (int)(il & 1);
+            const AccPlan ap = acc_plan<NCLS, HALF>(est, ig.N);
             if (etid == 0) {
-                if (!mbar_wait(smem_u32(&bTFull[set]), (uint32_t)((il / NSETS) & 1), kWaitLimitNs) ||
-                    !mbar_wait(smem_u32(&bMFull[slot]), (uint32_t)((il >> 1) & 1), kWaitLimitNs))
-                    sFail = 1;
+                for (int h = ap.h0; h < ap.h0 + ap.nh; ++h)
+                    if (!mbar_wait(smem_u32(&bTFull[h]), (uint32_t)(est.uses[h] & 1), kWaitLimitNs)) sFail = 1;
+                if (!mbar_wait(smem_u32(&bMFull[slot]), (uint32_t)((il >> 1) & 1), kWaitLimitNs)) sFail = 1;
             }
             group_sync(kBarEpi, kEpiThreads);
             if (sFail) break;
             tc_fence_after();
             const ItemMeta& mt = sMeta[slot];
             const int gm = mt.gcol[0][m], Ea = mt.E[0][m];
-            const uint32_t tbase = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(set * NCLS * kST);
+            const uint32_t tbase = tmem + ((uint32_t)(32 * quad) << 16) + ap.base;
 #pragma unroll 1
             for (int h = 0; h < kEpiCols / 8; ++h) {
                 const int n0 = kEpiCols * part + 8 * h;
@@ -605,7 +639,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                 // beyond N, or wholly below the diagonal of a diagonal tile
                 if (32 * quad >= ig.wa || n0 >= ig.N || (ig.diag && n0 + 7 < 32 * quad)) continue;
                 float cv[NCLS][8];
-                tmem_load_classes<NCLS>(tbase + (uint32_t)n0, cv);
+                tmem_load_classes<NCLS>(tbase + (uint32_t)n0, (uint32_t)ap.cs, cv);
                 if (gm < 0 || Ea == kNone) continue;
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -631,12 +665,14 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
             tc_fence_before();
             group_sync(kBarEpi, kEpiThreads);                 // the accumulators and the metadata are read
             if (etid == 0) {
-                mbar_arrive(smem_u32(&bTEmpty[set]));
+                for (int h = ap.h0; h < ap.h0 + ap.nh; ++h) mbar_arrive(smem_u32(&bTEmpty[h]));
                 mbar_arrive(smem_u32(&bMEmpty[slot]));
             }
+            for (int h = ap.h0; h < ap.h0 + ap.nh; ++h) ++est.uses[h];
         }
     } else {
         // ======================= MMA issuer (one lane) ===========================
+        AccState mst{0, {0, 0}};
         int chunk_no = 0;
         uint32_t last_bar = 0, last_parity = 0;
         bool issued = false;
@@ -645,13 +681,14 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
             const GramTcGroup gr = g.groups[it.group];
             const ItemGeo ig = item_geo<SYM, SAME, ROWS>(it, gr);
             if (!ig.ok) continue;
-            const int set = (int)(il % NSETS);
+            const AccPlan ap = acc_plan<NCLS, HALF>(mst, ig.N);
             bool fail = false;
             if (lane == 0) {
-                fail = !mbar_wait(smem_u32(&bTEmpty[set]), (uint32_t)(((il / NSETS) & 1) ^ 1), kWaitLimitNs);
+                for (int h = ap.h0; h < ap.h0 + ap.nh && !fail; ++h)
+                    fail = !mbar_wait(smem_u32(&bTEmpty[h]), (uint32_t)((mst.uses[h] & 1) ^ 1), kWaitLimitNs);
                 if (!fail) tc_fence_after();
                 const uint32_t idesc = bf16_idesc(128, ig.N);
-                const uint32_t dset = tmem + (uint32_t)(set * NCLS * kST);
+                const uint32_t dset = tmem + ap.base;
                 bool started[NCLS];
 #pragma unroll
                 for (int k = 0; k < NCLS; ++k) started[k] = false;
@@ -674,7 +711,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
 #pragma unroll
                             for (int kk = 0; kk < kKC / 16; ++kk) {
                                 // the first product of each class in the item starts its sum
-                                mma_bf16(dset + (uint32_t)(cls * kST), sw128_desc(a0 + (s - 1) * kPanel + 32 * kk),
+                                mma_bf16(dset + (uint32_t)(cls * ap.cs), sw128_desc(a0 + (s - 1) * kPanel + 32 * kk),
                                          sw128_desc(b0 + (t - 1) * kPanel + 32 * kk), idesc, started[cls] ? 1u : 0u);
                                 started[cls] = true;
                             }
@@ -685,12 +722,15 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                     issued = true;
                 }
                 if (!fail) {
-                    mma_commit(smem_u32(&bTFull[set]));
-                    last_bar = smem_u32(&bTFull[set]);
-                    last_parity = (uint32_t)((il / NSETS) & 1);
+                    for (int h = ap.h0; h < ap.h0 + ap.nh; ++h) {
+                        mma_commit(smem_u32(&bTFull[h]));
+                        last_bar = smem_u32(&bTFull[h]);
+                        last_parity = (uint32_t)(mst.uses[h] & 1);
+                    }
                 }
                 if (fail) sFail = 1;
             }
+            for (int h = ap.h0; h < ap.h0 + ap.nh; ++h) ++mst.uses[h];
             __syncwarp();
             if (sFail) break;
         }
@@ -728,12 +768,12 @@ cudaError_t mirror_upper(double* G, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS, int PW>
+template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS, int PW, bool HALF>
 cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
     constexpr int smem = 2 * kStage + 1024;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW>,
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW, HALF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
@@ -746,7 +786,7 @@ cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<int64_t>(g.n_items, (int64_t)sms);
-    gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW><<<grid, kThreads, smem, s>>>(g);
+    gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW, HALF><<<grid, kThreads, smem, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -766,17 +806,17 @@ cudaError_t launch_gram_tc(const GramTcArgs& g, GramMode mode, cudaStream_t s) {
             o.items = g.items + g.n_items_diag;
             o.item_exp = g.item_exp + g.n_items_diag * 2 * kST;
             o.n_items = g.n_items - g.n_items_diag;
-            cudaError_t e = launch_tc<5, 5, 6, 4, true, true, false, 2, kItemRowsPP, 8>(d, s);
-            if (e == cudaSuccess) e = launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP, 8>(o, s);
+            cudaError_t e = launch_tc<5, 5, 6, 4, true, true, false, 2, kItemRowsPP, 8, true>(d, s);
+            if (e == cudaSuccess) e = launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP, 8, false>(o, s);
             if (e == cudaSuccess) e = mirror_upper(g.G, g.n_cols, s);
             return e;
         }
         case GramMode::PtYSym: {
-            cudaError_t e = launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY, 16>(g, s);
+            cudaError_t e = launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY, 16, false>(g, s);
             if (e == cudaSuccess) e = mirror_upper(g.G, g.n_cols, s);
             return e;
         }
-        default: return launch_tc<3, 3, 4, 2, false, false, true, 2, kItemRowsPY, 16>(g, s);
+        default: return launch_tc<3, 3, 4, 2, false, false, true, 2, kItemRowsPY, 16, false>(g, s);
     }
 }
 

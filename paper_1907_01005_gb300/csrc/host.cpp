@@ -991,6 +991,13 @@ int fe_bcsr_create(const fe_mesh* m, int32_t n_cols, int32_t ncb, const int32_t*
             window_major(b->tc_ps, 0, b->tc_ps.size());
             window_major(b->tc_pp, 0, b->tc_pp.size());
             window_major(pp_off, 0, pp_off.size());
+            // diagonal P^T P tiles of at most half the tile width first: their
+            // accumulators take half the tensor memory, so consecutive ones
+            // overlap (each CTA takes its share of them in a row)
+            std::stable_partition(b->tc_pp.begin(), b->tc_pp.end(), [&](const GramTcItem& it) {
+                const int mi = it.tile & 0xffff;
+                return std::min(gram_tc_tile(), b->tc_groups[it.group].width - mi * gram_tc_tile()) <= gram_tc_tile() / 2;
+            });
             b->n_pp_diag = (int64_t)b->tc_pp.size();
             b->tc_pp.insert(b->tc_pp.end(), pp_off.begin(), pp_off.end());
             b->tc_rows.resize(R);
