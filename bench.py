@@ -314,8 +314,10 @@ _SRC_APPLY = ("apply_unit.cu", "unit_common.cuh")
 _SRC_MMULT = ("mmult_tc.cu", "tc_common.cuh")
 NCU_TRAFFIC = {
     # P^T Y (symmetric form) and P^T P (diagonal + off-diagonal tiles)
-    "gram_py": (_SRC_GRAM, "aadc0a7a6e36453952ad4bf74bcb7745a2158160d3a2599b82d6245f570c4385", 513266432),
-    "gram_pp": (_SRC_GRAM, "aadc0a7a6e36453952ad4bf74bcb7745a2158160d3a2599b82d6245f570c4385", 280160768),
+    "gram_py": (_SRC_GRAM, "f530cbbcdb5087671848cea51eff40c662adca1893ce0bc5ca1a68a6fd5a2e1f", 513432064),
+    "gram_pp": (_SRC_GRAM, "f530cbbcdb5087671848cea51eff40c662adca1893ce0bc5ca1a68a6fd5a2e1f", 277812480),
+    # post-multiplication with beta = 1 (the second OM call: A and C read, C written)
+    "mmult": (_SRC_MMULT, "7d3ba5b905daeb249bc2c98c043408c2e09233844b13a47f2fed7b0ae2c1faa9", 712096512),
     "apply": (_SRC_APPLY, "dcc43559e402f7a95e266b012ea5ce4ed2b7bb1a70b25ce53a6455d603070966", 730593536),
 }
 
@@ -698,7 +700,10 @@ def main():
             "kernels": kernels, "roofline": roof, "step_hbm_roofline": step_roof,
             "alu_peaks_tflops": {"fp32": probe_alu(1) / 1e12, "fp32x2": probe_alu(3) / 1e12,
                                  "fp64": fp64_peak / 1e12},
-            "gpu_launches": 3 * args.steps, "clocks": clk}
+            # per step: the apply; P^T P's exponent pass and Gram kernel for the
+            # diagonal and for the off-diagonal tiles, and its mirror; the
+            # symmetric P^T Y's exponent pass, Gram kernel and mirror
+            "gpu_launches": 9 * args.steps, "clocks": clk}
 
     # the p = 4 paper-scale workload beside p = 2 (same DoFs and orbitals)
     if args.config == "p2" and not args.no_p4:
@@ -708,9 +713,12 @@ def main():
     om = time_om(pb, max(10, args.steps // 10))
     t_mm = om["mmult_1"] * 1e-3
     t_mm2 = om["mmult_2"] * 1e-3
-    om["mmult_roofline"] = {"bound": "alu", "achieved": info.gram_flops / t_mm / 1e12, "peak": fp32_peak / 1e12,
-                            "unit": "TFLOP/s", "frac": info.gram_flops / t_mm / fp32_peak,
-                            "hbm_frac": 2 * nnz * s / t_mm / 1e9 / hbm_peak,
+    # the tensor-core post-multiplication is bound by HBM: A read and C written
+    # (beta = 0), plus C read (beta = 1); its 3-term TF32 products take less
+    # time at the tensor peak than those bytes at the HBM peak
+    om["mmult_roofline"] = {"bound": "hbm", "achieved": 2 * nnz * s / t_mm / 1e9, "peak": hbm_peak,
+                            "unit": "GB/s", "frac": 2 * nnz * s / t_mm / 1e9 / hbm_peak,
+                            "gflops": info.gram_flops / t_mm / 1e9,
                             "traffic_beta1": ncu_traffic("mmult", cfg.name),
                             "hbm_frac_beta1": 3 * nnz * s / t_mm2 / 1e9 / hbm_peak}
     om["gradient_ms"] = ms_step + om["total_ms"]      # H P, Hbar, P^T P (the step) plus the above
