@@ -1,7 +1,9 @@
 """Launch shapes of the same step: persistent vs grid launch of the apply,
-the CUDA graph of the whole step, and the autotuner's choice all give the
-oracle's result within the parity tolerances, and agree with each other to
-the order of the FP additions in the scatter."""
+a cap on the SMs of the persistent launches, the CUDA graph of the whole
+step, and the autotuner's choice all give the oracle's result within the
+parity tolerances.  Y is written without atomics in a fixed order, so it is
+the same bit for bit under every launch shape; the Gram products differ only
+in the order of their FP64 atomic additions."""
 import json
 
 import numpy as np
@@ -45,16 +47,18 @@ def test_persistent_and_graph_match_oracle(name, dtype):
     tol = TOL[dtype]
     ref_py = r.G_PY[np.ix_(pb.perm, pb.perm)]
     ref_pp = r.G_PP[np.ix_(pb.perm, pb.perm)]
-    for knobs in [(1, 2, 0), (1, 8, 0), (0, 4, 1), (0, 4, 2)]:
+    for knobs, sm_cap in [((1, 2, 0), 0), ((1, 8, 0), 0), ((0, 4, 1), 0), ((0, 4, 2), 0), ((1, 4, 0), 7)]:
         pb.P.set_launch(*knobs)
+        pb.P.set_sm_limit(sm_cap)
         d["Y"].fill_(np.nan)
         apply_H_gram(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"])
         torch.cuda.synchronize()
         assert pb.mesh.check_device() == 0
         Y, PY, PP = _outputs(pb)
-        assert _relerr(Y, Y0) <= 10 * np.finfo(Y.dtype).eps, knobs
+        assert np.array_equal(Y, Y0), (knobs, sm_cap)
         assert _relerr(PY, ref_py) <= tol["PY"], knobs
         assert _relerr(PP, ref_pp) <= tol["PP"], knobs
+    pb.P.set_sm_limit(0)
     # graph of the step, launched twice on fresh garbage
     pb.P.set_launch(1, 4, 0)
     g = StepGraph(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"])
@@ -65,7 +69,7 @@ def test_persistent_and_graph_match_oracle(name, dtype):
         g.launch()
         torch.cuda.synchronize()
         Y, PY, PP = _outputs(pb)
-        assert _relerr(Y, Y0) <= 10 * np.finfo(Y.dtype).eps
+        assert np.array_equal(Y, Y0)
         assert _relerr(PY, ref_py) <= tol["PY"]
         assert _relerr(PP, ref_pp) <= tol["PP"]
     del g
@@ -122,8 +126,7 @@ def test_host_buffer_entry_matches_device_step(dtype, pinned):
     assert _relerr(G1.numpy(), r.G_PY[np.ix_(pb.perm, pb.perm)]) <= TOL[dtype]["PY"]
     assert _relerr(G2.numpy(), r.G_PP[np.ix_(pb.perm, pb.perm)]) <= TOL[dtype]["PP"]
     # a second call with P scaled by 2: every output follows (Y by 2, the Grams
-    # by 4), up to the order of the atomic additions into Y (FP32: ~1e-7 of Y,
-    # which P^T Y inherits) and into the Gram matrices
+    # by 4), up to the order of the atomic additions into the Gram matrices
     Y1, Gpy1, Gpp1 = Yh.numpy().copy(), G1.numpy().copy(), G2.numpy().copy()
     Ph.mul_(2)
     apply_H_gram_host(pb.mesh, pb.P, pb.Y, d["G_PY"], d["G_PP"], Ph, Yh, G1, G2)
