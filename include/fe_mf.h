@@ -331,6 +331,9 @@ int fe_trace_dot(const fe_bcsr* D, const fe_bcsr* G, double* out_dev, void* stre
  * Defaults: 0, 4, 0.  FE_EINVAL for values outside these ranges. */
 int fe_bcsr_set_launch(fe_bcsr* P, int32_t persistent, int32_t ctas_per_sm, int32_t cells_per_round);
 
+int fe_bcsr_get_launch(const fe_bcsr* P, int32_t* persistent, int32_t* ctas_per_sm,
+                       int32_t* cells_per_round);
+
 /* Caps the SMs that the persistent launches reading P may occupy: the
  * tensor-core Gram products (fe_gram_*, with P as A), the persistent apply
  * (fe_apply_H / fe_apply_M with P as source) and the tensor-core
@@ -340,8 +343,6 @@ int fe_bcsr_set_launch(fe_bcsr* P, int32_t persistent, int32_t ctas_per_sm, int3
  * its small ones the rest).  Results are unchanged.  FE_EINVAL for
  * max_sms < 0. */
 int fe_bcsr_set_sm_limit(fe_bcsr* P, int32_t max_sms);
-int fe_bcsr_get_launch(const fe_bcsr* P, int32_t* persistent, int32_t* ctas_per_sm,
-                       int32_t* cells_per_round);
 
 /* Declares (1) or withdraws (0, the default) that P's block pattern is closed
  * for the values P will hold: every row block that owns a node of a cell
