@@ -4,7 +4,9 @@ through the same fe_apply_H_gram call the benchmark times.
 
 The oracle cannot assemble and apply the whole operator quickly at this
 size, so Y is checked on sampled rows (each computed one by one from the
-cells around the node), P^T P against the oracle's full FP64 product, and
+cells around the node), among them rows on the patches' upper faces, edges
+and corners, which receive halo contributions from the neighbour patches;
+P^T P against the oracle's full FP64 product, and
 P^T Y on four or more column blocks (among them both ends of the widest
 union of a Gram work group), whose columns of Y the oracle computes from the
 rows of the pattern only.  Tolerances are the normwise bounds of the
@@ -92,10 +94,22 @@ def test_paper_scale(name, dtype):
     sample_rb = rng.choice(stored_rb, 40, replace=False)
     dofs = np.concatenate([rng.choice(np.arange(pb.rb_ptr[r], pb.rb_ptr[r + 1]), 3, replace=False)
                            for r in sample_rb])
+    # rows on the patches' upper faces, edges and corners: they receive the
+    # halo contributions of the upper neighbour patches (1, 3 or 7 of them)
+    q = 2 * cfg.p
+    shared = []
+    for r in sample_rb:
+        dd = np.arange(pb.rb_ptr[r], pb.rb_ptr[r + 1])
+        I, J, K = mesh.ijk(pb.keys[dd])
+        on = ((I % q == 0) & (I > 0)).astype(int) + ((J % q == 0) & (J > 0)) + ((K % q == 0) & (K > 0))
+        for lo in (1, 2, 3):
+            cand = dd[on >= lo]
+            if len(cand):
+                shared.append(int(rng.choice(cand)))
     big = [int(np.argmax(np.abs(v))) for v in mv.vals[:6]]
     key_to_dof = np.empty(mesh.n_nodes, np.int64)
     key_to_dof[pb.keys] = np.arange(len(pb.keys))
-    dofs = np.unique(np.concatenate([dofs, [key_to_dof[mv.keys[a][i]] for a, i in enumerate(big)]]))
+    dofs = np.unique(np.concatenate([dofs, shared, [key_to_dof[mv.keys[a][i]] for a, i in enumerate(big)]]))
     keys = pb.keys[dofs]
     ref_rows = O.apply_rows(mesh, O.potential_fn(cfg, fp32), Psp, keys)   # (HP)[keys, orbital]
     got, ref = [], []
