@@ -279,10 +279,13 @@ int fe_apply_H_gram(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_PY_de
  * P's values from P_host (value_bytes) into P's bound device array, runs
  * the step of fe_apply_H_gram, copies Y's values to Y_host and both Gram
  * matrices to G_PY_host / G_PP_host, and synchronises `stream`.  The copies
- * overlap the kernels where the data allows: G_PP leaves on P's side stream
- * after P^T P, and Y leaves on a second stream owned by P (created on the
- * first call, destroyed with P) while P^T Y runs.  Host buffers should be
- * pinned for full copy bandwidth and for the copies to run asynchronously. */
+ * overlap the kernels where the data allows: the apply runs as soon as P is
+ * in, then Y leaves on a second stream owned by P (created on the first
+ * call, destroyed with P) while P^T P (on P's side stream, G_PP leaving
+ * after it) and P^T Y run.  On an error of the apply the call synchronises
+ * `stream` and returns the apply's code; Y_host and the Gram buffers are
+ * then not written.  Host buffers should be pinned for full copy bandwidth
+ * and for the copies to run asynchronously. */
 int fe_apply_H_gram_host(fe_mesh* mesh, const fe_bcsr* P, fe_bcsr* Y, double* G_PY_dev,
                          double* G_PP_dev, const void* P_host, void* Y_host,
                          double* G_PY_host, double* G_PP_host, void* stream);

@@ -1466,26 +1466,30 @@ int fe_apply_H_gram_host(fe_mesh* m, const fe_bcsr* P, fe_bcsr* Y, double* G_PY,
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vb = (size_t)P->n_values * P->elem();
     const size_t gb = (size_t)P->n_cols * P->n_cols * sizeof(double);
-    // P in; then P^T P (and its copy out) on the side stream beside the apply;
-    // Y out on the copy stream while P^T Y runs; G_PY out on `stream`
+    // The path through the step is P in, the apply, Y out: each of the two
+    // copies takes longer than both Gram products together.  So the apply
+    // runs alone right after P is in (a P^T P launched beside it would hold
+    // the SMs first and delay Y), and both Gram products run while Y goes
+    // out on the copy stream: P^T P on the side stream, P^T Y on `stream`.
     FE_TRY_CUDA(cudaMemcpyAsync(P->values, P_host, vb, cudaMemcpyHostToDevice, s), "fe_apply_H_gram_host: copy P in");
-    FE_TRY_CUDA(cudaEventRecord(Pm->ev_fork, s), "fe_apply_H_gram_host: fork");
-    FE_TRY_CUDA(cudaStreamWaitEvent(Pm->side, Pm->ev_fork, 0), "fe_apply_H_gram_host: fork");
+    rc = fe_apply_H(m, P, Y, stream);
+    if (rc != FE_OK) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    FE_TRY_CUDA(cudaEventRecord(Pm->ev_y, s), "fe_apply_H_gram_host: Y ready");
+    FE_TRY_CUDA(cudaStreamWaitEvent(Pm->copy, Pm->ev_y, 0), "fe_apply_H_gram_host: Y ready");
+    FE_TRY_CUDA(cudaMemcpyAsync(Y_host, Y->values, vb, cudaMemcpyDeviceToHost, Pm->copy), "fe_apply_H_gram_host: copy Y out");
+    FE_TRY_CUDA(cudaEventRecord(Pm->ev_copied, Pm->copy), "fe_apply_H_gram_host: Y copied");
+    FE_TRY_CUDA(cudaStreamWaitEvent(Pm->side, Pm->ev_y, 0), "fe_apply_H_gram_host: fork");
     const int rc_pp = fe_gram_PtP(P, G_PP, Pm->side);
     if (rc_pp == FE_OK)
         FE_TRY_CUDA(cudaMemcpyAsync(G_PP_host, G_PP, gb, cudaMemcpyDeviceToHost, Pm->side), "fe_apply_H_gram_host: copy G_PP out");
     FE_TRY_CUDA(cudaEventRecord(Pm->ev_join, Pm->side), "fe_apply_H_gram_host: join");
-    rc = fe_apply_H(m, P, Y, stream);
-    if (rc == FE_OK) {
-        FE_TRY_CUDA(cudaEventRecord(Pm->ev_y, s), "fe_apply_H_gram_host: Y ready");
-        FE_TRY_CUDA(cudaStreamWaitEvent(Pm->copy, Pm->ev_y, 0), "fe_apply_H_gram_host: Y ready");
-        FE_TRY_CUDA(cudaMemcpyAsync(Y_host, Y->values, vb, cudaMemcpyDeviceToHost, Pm->copy), "fe_apply_H_gram_host: copy Y out");
-        FE_TRY_CUDA(cudaEventRecord(Pm->ev_copied, Pm->copy), "fe_apply_H_gram_host: Y copied");
-        rc = gram_pty("fe_apply_H_gram_host", P, Y, G_PY, P->closed != 0, s);
-        if (rc == FE_OK)
-            FE_TRY_CUDA(cudaMemcpyAsync(G_PY_host, G_PY, gb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy G_PY out");
-        FE_TRY_CUDA(cudaStreamWaitEvent(s, Pm->ev_copied, 0), "fe_apply_H_gram_host: join copy");
-    }
+    rc = gram_pty("fe_apply_H_gram_host", P, Y, G_PY, P->closed != 0, s);
+    if (rc == FE_OK)
+        FE_TRY_CUDA(cudaMemcpyAsync(G_PY_host, G_PY, gb, cudaMemcpyDeviceToHost, s), "fe_apply_H_gram_host: copy G_PY out");
+    FE_TRY_CUDA(cudaStreamWaitEvent(s, Pm->ev_copied, 0), "fe_apply_H_gram_host: join copy");
     FE_TRY_CUDA(cudaStreamWaitEvent(s, Pm->ev_join, 0), "fe_apply_H_gram_host: join");
     FE_TRY_CUDA(cudaStreamSynchronize(s), "fe_apply_H_gram_host: synchronize");
     return rc != FE_OK ? rc : rc_pp;
