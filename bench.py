@@ -437,7 +437,11 @@ def kernel_rooflines(cfg, pb, per, ms_step, hbm_peak, peak_src, fp32_peak):
             "traffic": ncu_traffic(dom, cfg.name),
             "peak_source": (f"{peak_src} hbm_gbs" if kd["roof_bound"] == "hbm" else
                             "measured fp32 FMA probe" if kd["roof_bound"] == "alu" else "measured bf16_tflops"),
-            "per_launch": "achieved = algorithmic bytes (stored entries x 4 B) / CUDA-event median"}
+            "per_launch": {"hbm": "achieved = algorithmic bytes of one launch / its CUDA-event median",
+                           "alu": "achieved = algorithmic flops of one launch (active cell-columns x "
+                                  "(18 n^4 + 3 n^3)) / its CUDA-event median",
+                           "tensor": "achieved = bf16 slice-product flops of one launch / its CUDA-event median"
+                           }[kd["roof_bound"]]}
     step_bytes = apply_bytes + py_bytes + pp_bytes
     step_roof = {"bytes": step_bytes, "ideal_ms": step_bytes / (hbm_peak * 1e9) * 1e3,
                  "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak}

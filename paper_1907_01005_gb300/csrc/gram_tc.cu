@@ -202,8 +202,23 @@ __device__ __forceinline__ Quad quad_unpack(int q) {
     return Quad{q & 63, (q >> 6) & 31, (q >> 11) & 255, (q >> 19) & 15, ((q >> 23) & 255) - 4};
 }
 
+// Rounding to a fixed grid with two additions: for |r| < 2^(k-1), (r + C) - C
+// with C = 1.5 2^(k+23) is r rounded to the nearest multiple of 2^k, ties to
+// even, as rint(r 2^-k) 2^k (the sum stays in C's binade, whose unit in the
+// last place is 2^k, and the difference is exact).  __fadd_rn / __fsub_rn
+// keep the compiler from contracting or reassociating the pair.
+__device__ __forceinline__ float grid_c(int k) { return __int_as_float(((127 + k + 23) << 23) | 0x400000); }
+__device__ __forceinline__ float round_to_grid(float r, float c) { return __fsub_rn(__fadd_rn(r, c), c); }
+// Two floats with at most 8 significant bits (exact in bf16) as a bf16 pair,
+// a in the low half: their upper 16 bits.
+__device__ __forceinline__ uint32_t bf16_pair_exact(float a, float b) {
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
 // Slices 8 values (already multiplied by f1) of operand row c into S bf16
-// slices y_s = q_s 2^(-8 s) on fixed grids, one 16-byte chunk per slice panel.
+// slices y_s = q_s 2^(-8 s) on fixed grids, one 16-byte chunk per slice panel:
+// y_s is the residual rounded to the grid 2^(-8 s), the residual loses it
+// (exactly), and |q_s| <= 2^8 makes y_s exact in bf16.
 template <int S>
 __device__ __forceinline__ void slice_store(unsigned char* base, int c, int j, float f2, const float (&v)[8]) {
     float r[8];
@@ -212,15 +227,14 @@ __device__ __forceinline__ void slice_store(unsigned char* base, int c, int j, f
     const uint32_t off = sw_off(c, j);
 #pragma unroll
     for (int s = 1; s <= S; ++s) {
-        const float up = pow2f(8 * s), dn = pow2f(-8 * s);
+        const float cs = grid_c(-8 * s);
         uint32_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float q0 = rintf(r[2 * i] * up), q1 = rintf(r[2 * i + 1] * up);
-            r[2 * i] = fmaf(-q0, dn, r[2 * i]);
-            r[2 * i + 1] = fmaf(-q1, dn, r[2 * i + 1]);
-            const __nv_bfloat162 b = __floats2bfloat162_rn(q0 * dn, q1 * dn);   // exact
-            w[i] = *reinterpret_cast<const uint32_t*>(&b);
+            const float y0 = round_to_grid(r[2 * i], cs), y1 = round_to_grid(r[2 * i + 1], cs);
+            r[2 * i] = __fsub_rn(r[2 * i], y0);
+            r[2 * i + 1] = __fsub_rn(r[2 * i + 1], y1);
+            w[i] = bf16_pair_exact(y0, y1);
         }
         *reinterpret_cast<uint4*>(base + (s - 1) * kPanel + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -230,19 +244,19 @@ __device__ __forceinline__ void slice_store(unsigned char* base, int c, int j, f
 // y2 = bf16(x - y1), y3 = bf16(x - y1 - y2).
 __device__ __forceinline__ void slice_store_nat(unsigned char* base, int c, int j, float f2, const float (&v)[8]) {
     const uint32_t off = sw_off(c, j);
+    const float c1 = grid_c(-8);
     uint32_t w1[4], w2[4], w3[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float r0 = v[2 * i] * f2, r1 = v[2 * i + 1] * f2;
-        const float q0 = rintf(r0 * 256.f), q1 = rintf(r1 * 256.f);
-        r0 = fmaf(-q0, 0.00390625f, r0);
-        r1 = fmaf(-q1, 0.00390625f, r1);
-        const __nv_bfloat162 b1 = __floats2bfloat162_rn(q0 * 0.00390625f, q1 * 0.00390625f);   // exact
+        const float y0 = round_to_grid(r0, c1), y1 = round_to_grid(r1, c1);
+        r0 = __fsub_rn(r0, y0);
+        r1 = __fsub_rn(r1, y1);
+        w1[i] = bf16_pair_exact(y0, y1);
         const __nv_bfloat162 b2 = __floats2bfloat162_rn(r0, r1);
         r0 -= __low2float(b2);
         r1 -= __high2float(b2);
         const __nv_bfloat162 b3 = __floats2bfloat162_rn(r0, r1);
-        w1[i] = *reinterpret_cast<const uint32_t*>(&b1);
         w2[i] = *reinterpret_cast<const uint32_t*>(&b2);
         w3[i] = *reinterpret_cast<const uint32_t*>(&b3);
     }
