@@ -494,6 +494,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
     __shared__ volatile int sFail;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // a kernel launched after this one as dependent may start its CTAs as SMs
+    // free up (it reads nothing this kernel writes)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bFull[b])) : "memory");
@@ -782,26 +785,48 @@ cudaError_t mirror_upper(double* G, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The item exponents of g's items: one CTA per item.
+template <bool SYM, bool SAME, int ROWS>
+cudaError_t launch_exp(const GramTcArgs& g, cudaStream_t s) {
+    if (g.n_items == 0) return cudaSuccess;
+    gram_exp_kernel<SYM, SAME, ROWS><<<(unsigned)g.n_items, kGroupThreads, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+// The persistent Gram kernel over g's items (their exponents computed before).
+// dependent: launched with programmatic stream serialisation, so that its
+// CTAs take the SMs that the previous kernel's CTAs leave while the rest of
+// that kernel still runs (the previous kernel triggers at its start).  Only
+// for a kernel that reads nothing the previous one writes.
 template <int SA, int SB, int LMAX, int NCLS, bool SYM, bool SAME, bool NAT, int NST, int ROWS, int PW, bool HALF>
-cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s) {
+cudaError_t launch_tc(const GramTcArgs& g, cudaStream_t s, bool dependent = false) {
     constexpr int smem = 2 * kStage + 1024;
+    auto kern = gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW, HALF>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW, HALF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     if (g.n_items == 0) return cudaSuccess;
     const int sms = usable_sms(g.sm_limit);
     if (sms < 1) return cudaErrorInvalidDevice;
-    // the item exponents first (one CTA per item), then the persistent kernel
-    gram_exp_kernel<SYM, SAME, ROWS><<<(unsigned)g.n_items, kGroupThreads, 0, s>>>(g);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<int64_t>(g.n_items, (int64_t)sms);
-    gram_tc_kernel<SA, SB, LMAX, NCLS, SYM, SAME, NAT, NST, ROWS, PW, HALF><<<grid, kThreads, smem, s>>>(g);
-    return cudaGetLastError();
+    if (!dependent) {
+        kern<<<grid, kThreads, smem, s>>>(g);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, g);
 }
 
 }  // namespace
@@ -820,17 +845,27 @@ cudaError_t launch_gram_tc(const GramTcArgs& g, GramMode mode, cudaStream_t s) {
             o.items = g.items + g.n_items_diag;
             o.item_exp = g.item_exp + g.n_items_diag * 2 * kST;
             o.n_items = g.n_items - g.n_items_diag;
-            cudaError_t e = launch_tc<5, 5, 6, 4, true, true, false, 2, kItemRowsPP, 8, true>(d, s);
-            if (e == cudaSuccess) e = launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP, 8, false>(o, s);
+            // both exponent passes first; the off-diagonal tiles then fill the
+            // SMs that the diagonal kernel's CTAs leave as they finish
+            cudaError_t e = launch_exp<true, true, kItemRowsPP>(d, s);
+            if (e == cudaSuccess) e = launch_exp<true, false, kItemRowsPP>(o, s);
+            if (e == cudaSuccess) e = launch_tc<5, 5, 6, 4, true, true, false, 2, kItemRowsPP, 8, true>(d, s);
+            if (e == cudaSuccess)
+                e = launch_tc<5, 5, 6, 4, true, false, false, 1, kItemRowsPP, 8, false>(o, s, d.n_items > 0);
             if (e == cudaSuccess) e = mirror_upper(g.G, g.n_cols, s);
             return e;
         }
         case GramMode::PtYSym: {
-            cudaError_t e = launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY, 16, false>(g, s);
+            cudaError_t e = launch_exp<true, false, kItemRowsPY>(g, s);
+            if (e == cudaSuccess) e = launch_tc<3, 3, 4, 2, true, false, true, 2, kItemRowsPY, 16, false>(g, s);
             if (e == cudaSuccess) e = mirror_upper(g.G, g.n_cols, s);
             return e;
         }
-        default: return launch_tc<3, 3, 4, 2, false, false, true, 2, kItemRowsPY, 16, false>(g, s);
+        default: {
+            cudaError_t e = launch_exp<false, false, kItemRowsPY>(g, s);
+            if (e == cudaSuccess) e = launch_tc<3, 3, 4, 2, false, false, true, 2, kItemRowsPY, 16, false>(g, s);
+            return e;
+        }
     }
 }
 
