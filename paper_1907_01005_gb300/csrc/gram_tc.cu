@@ -159,10 +159,11 @@ __device__ __forceinline__ long long round_scaled_i64(float v) {
 // Loads rows kstart .. kstart+7 of the group (those at or past kend read as
 // zero) of one 16-byte quad of a union block (slot u, block columns a0 ..
 // a0 + 3; consecutive rows of a row block are ld elements apart) as float4.
-__device__ __forceinline__ void load8q(const float* __restrict__ X, int u, int a0, int ld, const int64_t* sOff,
-                                       int n_u, const int* sPref, int nrb, int kstart, int kend, float4 (&v)[8]) {
+template <int R>
+__device__ __forceinline__ void loadq(const float* __restrict__ X, int u, int a0, int ld, const int64_t* sOff,
+                                      int n_u, const int* sPref, int nrb, int kstart, int kend, float4 (&v)[R]) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < R; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (kstart >= kend) return;
     int r = 0;
     while (r < nrb - 1 && kstart >= sPref[r + 1]) ++r;
@@ -170,7 +171,7 @@ __device__ __forceinline__ void load8q(const float* __restrict__ X, int u, int a
     int64_t o = sOff[r * n_u + u];
     int64_t idx = o + (int64_t)(kstart - sPref[r]) * ld + a0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < R; ++i) {
         const int k = kstart + i;
         if (k < kend) {
             if (k == e) {                     // first row of the next row block (k < kend <= sPref[nrb])
@@ -183,6 +184,11 @@ __device__ __forceinline__ void load8q(const float* __restrict__ X, int u, int a
             idx += ld;
         }
     }
+}
+
+__device__ __forceinline__ void load8q(const float* __restrict__ X, int u, int a0, int ld, const int64_t* sOff,
+                                       int n_u, const int* sPref, int nrb, int kstart, int kend, float4 (&v)[8]) {
+    loadq<8>(X, u, a0, ld, sOff, n_u, sPref, nrb, kstart, kend, v);
 }
 
 // Component i of a float4
@@ -219,24 +225,30 @@ __device__ __forceinline__ uint32_t bf16_pair_exact(float a, float b) {
 // slices y_s = q_s 2^(-8 s) on fixed grids, one 16-byte chunk per slice panel:
 // y_s is the residual rounded to the grid 2^(-8 s), the residual loses it
 // (exactly), and |q_s| <= 2^8 makes y_s exact in bf16.
-template <int S>
-__device__ __forceinline__ void slice_store(unsigned char* base, int c, int j, float f2, const float (&v)[8]) {
-    float r[8];
+// R = 8 values fill the 16-byte chunk j of the row; R = 4 values the half
+// h & 1 of chunk h >> 1 (j = h).
+template <int S, int R = 8>
+__device__ __forceinline__ void slice_store(unsigned char* base, int c, int j, float f2, const float (&v)[R]) {
+    static_assert(R == 8 || R == 4, "a 16-byte chunk or half of one");
+    float r[R];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) r[i] = v[i] * f2;
-    const uint32_t off = sw_off(c, j);
+    for (int i = 0; i < R; ++i) r[i] = v[i] * f2;
+    const uint32_t off = R == 8 ? sw_off(c, j) : sw_off(c, j >> 1) + 8u * (uint32_t)(j & 1);
 #pragma unroll
     for (int s = 1; s <= S; ++s) {
         const float cs = grid_c(-8 * s);
-        uint32_t w[4];
+        uint32_t w[R / 2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < R / 2; ++i) {
             const float y0 = round_to_grid(r[2 * i], cs), y1 = round_to_grid(r[2 * i + 1], cs);
             r[2 * i] = __fsub_rn(r[2 * i], y0);
             r[2 * i + 1] = __fsub_rn(r[2 * i + 1], y1);
             w[i] = bf16_pair_exact(y0, y1);
         }
-        *reinterpret_cast<uint4*>(base + (s - 1) * kPanel + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        if constexpr (R == 8)
+            *reinterpret_cast<uint4*>(base + (s - 1) * kPanel + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        else
+            *reinterpret_cast<uint2*>(base + (s - 1) * kPanel + off) = make_uint2(w[0], w[1]);
     }
 }
 
@@ -482,6 +494,11 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
     constexpr int kEpiCols = kST / (EW / 4);                   // tile columns of an epilogue warp
     static_assert(NCLS * kST <= 512, "tensor memory: 128 columns per level class");
     constexpr int U = 8 * LMAX;                 // the epilogue works in units of 2^-U
+    // staging task: one quad x RT rows.  P^T P diagonal tiles (one panel, five
+    // slices) take 4-row tasks, twice as many, so that the group's threads
+    // share them more evenly; the others 8-row tasks
+    constexpr int RT = (SAME && !NAT) ? 4 : 8;
+    constexpr int kTpq = kKC / RT;              // tasks per quad and chunk
     constexpr int bytesA = SA * kPanel, bytesB = SB * kPanel;
     static_assert(NST == 2 ? (SAME ? bytesA : bytesA + bytesB) <= kStage : bytesA + bytesB <= 2 * kStage,
                   "a chunk fits its stage");
@@ -590,30 +607,34 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                 unsigned char* bufA = ring + stage * kStage;
                 unsigned char* bufB = SAME ? bufA : bufA + bytesA;
                 const int c0 = it.k0 + kKC * j, c1 = min(it.k1, c0 + kKC);
-                for (int side = 0; side < nsides; ++side) {
-                    const float* X = side ? g.B : g.A;
-                    unsigned char* base = side ? bufB : bufA;
-                    const int nq = T.nq[side];
+                {
                     // operand rows beyond the tile's columns are never read back:
-                    // they are left as they are.  Neighbouring threads take the
-                    // eight 8-row groups of a quad, so that the 16-byte slice
-                    // stores of a warp land in all eight chunk positions of the
-                    // swizzled rows (no bank conflicts).
-                    for (int t = gt; t < nq * 8; t += kGroupThreads) {
-                        const Quad qd = quad_unpack(T.quad[side][t >> 3]);
-                        const int jj = t & 7;
-                        float4 v[8];
-                        load8q(X, qd.u, qd.a0, qd.ld, T.off, gr.n_u, T.pref, ig.nrb, c0 + 8 * jj, c1, v);
+                    // they are left as they are.  Tasks are (quad, RT-row group),
+                    // the A side's then the B side's in one range, so that the
+                    // group's threads share both sides' tasks evenly.
+                    // Neighbouring threads take the row groups of a quad, so
+                    // that the slice stores of a warp (16 or 8 bytes each) cover
+                    // whole 128-byte swizzled rows (no bank conflicts).
+                    const int nt0 = kTpq * T.nq[0], nt = nt0 + (nsides > 1 ? kTpq * T.nq[1] : 0);
+                    for (int t = gt; t < nt; t += kGroupThreads) {
+                        const int side = t >= nt0 ? 1 : 0;
+                        const int ts = t - side * nt0;
+                        const float* X = side ? g.B : g.A;
+                        unsigned char* base = side ? bufB : bufA;
+                        const Quad qd = quad_unpack(T.quad[side][ts / kTpq]);
+                        const int jj = ts % kTpq;
+                        float4 v[RT];
+                        loadq<RT>(X, qd.u, qd.a0, qd.ld, T.off, gr.n_u, T.pref, ig.nrb, c0 + RT * jj, c1, v);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             if (!((qd.mask >> i) & 1)) continue;
                             const int tc = qd.tc0 + i;
                             const float f1 = T.f1[side][tc], f2 = T.f2[side][tc];
-                            float x[8];
+                            float x[RT];
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) x[k] = f4c(v[k], i) * f1;
+                            for (int k = 0; k < RT; ++k) x[k] = f4c(v[k], i) * f1;
                             if constexpr (NAT) slice_store_nat(base, tc, jj, f2, x);
-                            else slice_store<(SA > SB ? SA : SB)>(base, tc, jj, f2, x);
+                            else slice_store<(SA > SB ? SA : SB), RT>(base, tc, jj, f2, x);
                         }
                     }
                 }
