@@ -314,8 +314,8 @@ _SRC_APPLY = ("apply_unit.cu", "unit_common.cuh")
 _SRC_MMULT = ("mmult_tc.cu", "tc_common.cuh")
 NCU_TRAFFIC = {
     # P^T Y (symmetric form) and P^T P (diagonal + off-diagonal tiles)
-    "gram_py": (_SRC_GRAM, "f530cbbcdb5087671848cea51eff40c662adca1893ce0bc5ca1a68a6fd5a2e1f", 513432064),
-    "gram_pp": (_SRC_GRAM, "f530cbbcdb5087671848cea51eff40c662adca1893ce0bc5ca1a68a6fd5a2e1f", 277812480),
+    "gram_py": (_SRC_GRAM, "661e14eaa15fd50eb4a93fadb0117c82aa8614447c6d9c3f34bbb7f15245ca96", 513113600),
+    "gram_pp": (_SRC_GRAM, "661e14eaa15fd50eb4a93fadb0117c82aa8614447c6d9c3f34bbb7f15245ca96", 277511936),
     # post-multiplication with beta = 1 (the second OM call: A and C read, C written)
     "mmult": (_SRC_MMULT, "7d3ba5b905daeb249bc2c98c043408c2e09233844b13a47f2fed7b0ae2c1faa9", 712096512),
     "apply": (_SRC_APPLY, "dcc43559e402f7a95e266b012ea5ce4ed2b7bb1a70b25ce53a6455d603070966", 730593536),
