@@ -172,7 +172,7 @@ cudaError_t probe_fma(int dtype, int64_t iters, double* flops_per_s, cudaStream_
 // in time (other streams, other host threads) write the same slots, which is
 // harmless for the probe's result but is a race on the array's contents.
 // ---------------------------------------------------------------------------
-__device__ __align__(256) double g_probe_sink[kProbeSinkSlots];
+static __device__ __align__(256) double g_probe_sink[kProbeSinkSlots];
 
 namespace {
 constexpr int kMaxDevices = 64;
