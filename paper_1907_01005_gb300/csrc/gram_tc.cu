@@ -186,6 +186,36 @@ __device__ __forceinline__ void loadq(const float* __restrict__ X, int u, int a0
     }
 }
 
+// Sources of rows kstart .. kstart+R-1 of one quad (as loadq): nullptr for
+// rows at or past kend and for absent blocks (read as zero).
+template <int R>
+__device__ __forceinline__ void quad_row_srcs(const float* __restrict__ X, int u, int a0, int ld, const int64_t* sOff,
+                                              int n_u, const int* sPref, int nrb, int kstart, int kend,
+                                              const float* (&src)[R]) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) src[i] = nullptr;
+    if (kstart >= kend) return;
+    int r = 0;
+    while (r < nrb - 1 && kstart >= sPref[r + 1]) ++r;
+    int e = sPref[r + 1];
+    int64_t o = sOff[r * n_u + u];
+    int64_t idx = o + (int64_t)(kstart - sPref[r]) * ld + a0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int k = kstart + i;
+        if (k < kend) {
+            if (k == e) {
+                ++r;
+                e = sPref[r + 1];
+                o = sOff[r * n_u + u];
+                idx = o + a0;
+            }
+            if (o >= 0) src[i] = X + idx;
+            idx += ld;
+        }
+    }
+}
+
 __device__ __forceinline__ void load8q(const float* __restrict__ X, int u, int a0, int ld, const int64_t* sOff,
                                        int n_u, const int* sPref, int nrb, int kstart, int kend, float4 (&v)[8]) {
     loadq<8>(X, u, a0, ld, sOff, n_u, sPref, nrb, kstart, kend, v);
@@ -502,6 +532,12 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
     constexpr int bytesA = SA * kPanel, bytesB = SB * kPanel;
     static_assert(NST == 2 ? (SAME ? bytesA : bytesA + bytesB) <= kStage : bytesA + bytesB <= 2 * kStage,
                   "a chunk fits its stage");
+    // One-panel tiles leave the last kStage - bytesA bytes of each stage
+    // unused by the MMAs.  There the producer keeps the raw FP32 rows of its
+    // tasks, fetched with cp.async one round of tasks ahead (round r of a
+    // chunk in the tail of stage r % 2, [row][thread] 16-byte slots), so the
+    // loads of the next round are in flight while the current one is sliced.
+    constexpr bool kRawPipe = SAME && NST == 2 && PW == 8 && kStage - bytesA >= RT * kGroupThreads * 16;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     unsigned char* ring = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
     __shared__ ItemTables sTab[2];                 // one per producer group
@@ -601,13 +637,56 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GramTcArgs g
                 if ((kAlt ? (chunk_no & 1) : 0) != grp) continue;
                 const int stage = NST == 2 ? (chunk_no & 1) : 0;
                 const int use = NST == 2 ? (chunk_no >> 1) : chunk_no;
+                const int c0 = it.k0 + kKC * j, c1 = min(it.k1, c0 + kKC);
+                // raw rows of task t into the tail of stage `buf` (this thread's slots)
+                auto raw_fetch = [&](int t, int buf) {
+                    const Quad qd = quad_unpack(T.quad[0][t / kTpq]);
+                    const float* src[RT];
+                    quad_row_srcs<RT>(g.A, qd.u, qd.a0, qd.ld, T.off, gr.n_u, T.pref, ig.nrb, c0 + RT * (t % kTpq),
+                                      c1, src);
+                    const uint32_t rb = smem_u32(ring + buf * kStage + bytesA) + 16u * (uint32_t)gt;
+#pragma unroll
+                    for (int i = 0; i < RT; ++i)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                                         rb + (uint32_t)(i * kGroupThreads * 16)),
+                                     "l"(src[i] ? src[i] : g.A), "r"(src[i] ? 16 : 0)
+                                     : "memory");
+                };
+                const int nt_raw = kTpq * T.nq[0];
+                if constexpr (kRawPipe) {
+                    if (gt < nt_raw) raw_fetch(gt, 0);
+                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                }
                 if (gt == 0 && !mbar_wait(smem_u32(&bEmpty[stage]), (use & 1) ^ 1, kWaitLimitNs)) sFail = 1;
                 group_sync(bar, kGroupThreads);
                 if (sFail) break;
                 unsigned char* bufA = ring + stage * kStage;
                 unsigned char* bufB = SAME ? bufA : bufA + bytesA;
-                const int c0 = it.k0 + kKC * j, c1 = min(it.k1, c0 + kKC);
-                {
+                if constexpr (kRawPipe) {
+                    for (int t = gt, r = 0; t < nt_raw; t += kGroupThreads, ++r) {
+                        if (t + kGroupThreads < nt_raw) raw_fetch(t + kGroupThreads, (r + 1) & 1);
+                        asm volatile("cp.async.commit_group;\n" ::: "memory");
+                        asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // round r has landed
+                        const Quad qd = quad_unpack(T.quad[0][t / kTpq]);
+                        const int jj = t % kTpq;
+                        const unsigned char* rb = ring + (r & 1) * kStage + bytesA + 16 * gt;
+                        float4 v[RT];
+#pragma unroll
+                        for (int i = 0; i < RT; ++i)
+                            v[i] = *reinterpret_cast<const float4*>(rb + i * kGroupThreads * 16);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (!((qd.mask >> i) & 1)) continue;
+                            const int tc = qd.tc0 + i;
+                            const float f1 = T.f1[0][tc], f2 = T.f2[0][tc];
+                            float x[RT];
+#pragma unroll
+                            for (int k = 0; k < RT; ++k) x[k] = f4c(v[k], i) * f1;
+                            slice_store<(SA > SB ? SA : SB), RT>(bufA, tc, jj, f2, x);
+                        }
+                    }
+                    asm volatile("cp.async.wait_all;\n" ::: "memory");
+                } else {
                     // operand rows beyond the tile's columns are never read back:
                     // they are left as they are.  Tasks are (quad, RT-row group),
                     // the A side's then the B side's in one range, so that the
