@@ -314,8 +314,8 @@ _SRC_APPLY = ("apply_unit.cu", "unit_common.cuh")
 _SRC_MMULT = ("mmult_tc.cu", "tc_common.cuh")
 NCU_TRAFFIC = {
     # P^T Y (symmetric form) and P^T P (diagonal + off-diagonal tiles)
-    "gram_py": (_SRC_GRAM, "661e14eaa15fd50eb4a93fadb0117c82aa8614447c6d9c3f34bbb7f15245ca96", 513113600),
-    "gram_pp": (_SRC_GRAM, "661e14eaa15fd50eb4a93fadb0117c82aa8614447c6d9c3f34bbb7f15245ca96", 277511936),
+    "gram_py": (_SRC_GRAM, "38f8f61988a3352f5b41e75a079c54aa342cc7618ddff5dd06381a995fbb7a45", 513261312),
+    "gram_pp": (_SRC_GRAM, "38f8f61988a3352f5b41e75a079c54aa342cc7618ddff5dd06381a995fbb7a45", 277447680),
     # post-multiplication with beta = 1 (the second OM call: A and C read, C written)
     "mmult": (_SRC_MMULT, "7d3ba5b905daeb249bc2c98c043408c2e09233844b13a47f2fed7b0ae2c1faa9", 712096512),
     "apply": (_SRC_APPLY, "dcc43559e402f7a95e266b012ea5ce4ed2b7bb1a70b25ce53a6455d603070966", 730593536),
